@@ -1,0 +1,16 @@
+"""CPU FP64 oracle for the tensor jump method (TJM) hot path.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously-correct
+reference that the CUDA path is checked against.  It shares no code with the
+CUDA library: only the tests, the smoke check and the benchmark's CPU-baseline
+leg may import it, and the product path never routes through it.
+
+Modules
+-------
+philox     Philox4x32-10 (SC'11 definition) and the (key, counter) layout.
+mps_tjm    O1: the MPS tensor jump method in FP64 (dissipative contraction,
+           stochastic jump, dynamic 1-/2-site TDVP with Lanczos exponentials,
+           sampling MPS), step by step in the paper's order.
+dense      O2: the same Strang-ordered jump schedule on a dense state vector,
+           and O3: the dense Lindblad master equation for small chains.
+"""

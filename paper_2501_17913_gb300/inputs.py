@@ -1,0 +1,184 @@
+"""Seeded synthetic workloads for the tensor jump method.
+
+This module only DESCRIBES problems -- Hamiltonian MPO tensors, jump-operator
+lists, initial product states, observables and output times -- with the
+shapes, sizes and parameter distributions of the paper's noisy spin-chain
+experiments.  It holds none of the method's arithmetic, so both the CUDA path
+(through the C ABI) and the CPU oracle (in the tests) take their inputs from it.
+
+Conventions (TJM, Sec. "Benchmarking"): |0> = (1, 0) has Z = +1 and is the
+relaxation target; sigma^- = [[0, 1], [0, 0]]; Z = diag(1, -1).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+I2 = np.eye(2, dtype=np.complex128)
+X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+SM = np.array([[0, 1], [0, 0]], dtype=np.complex128)   # sigma^- : |1> -> |0>
+SP = SM.T.copy()                                        # sigma^+ : |0> -> |1>
+
+
+def xxx_mpo(L: int, J: float = 1.0, g: float = 0.5):
+    """MPO (bond dimension 5) of H = J sum_i (X_i X_{i+1} + Y_i Y_{i+1} + Z_i Z_{i+1}) + g sum_i X_i.
+
+    XX + YY is written as 2 (sigma^+ sigma^- + sigma^- sigma^+), so every tensor
+    is real.  Site tensors have shape (D_left, D_right, 2, 2) with the first
+    physical index the output (bra) index; D_left = 1 on site 0 and
+    D_right = 1 on site L-1.
+    """
+    Wb = np.zeros((5, 5, 2, 2), dtype=np.complex128)
+    Wb[0, 0] = I2
+    Wb[0, 1] = 2 * J * SP
+    Wb[0, 2] = 2 * J * SM
+    Wb[0, 3] = J * Z
+    Wb[0, 4] = g * X
+    Wb[1, 4] = SM
+    Wb[2, 4] = SP
+    Wb[3, 4] = Z
+    Wb[4, 4] = I2
+    if L == 1:
+        return [Wb[0:1, 4:5].copy()]
+    W = [Wb[0:1, :].copy()]
+    W += [Wb.copy() for _ in range(L - 2)]
+    W.append(Wb[:, 4:5].copy())
+    return W
+
+
+def noise(L: int, gamma_relax: float = 0.1, gamma_dephase: float = 0.1):
+    """Relaxation sigma^- and dephasing Z on every site: [(site, op, rate)]."""
+    out = []
+    for l in range(L):
+        if gamma_relax > 0:
+            out.append((l, SM.copy(), float(gamma_relax)))
+    for l in range(L):
+        if gamma_dephase > 0:
+            out.append((l, Z.copy(), float(gamma_dephase)))
+    return out
+
+
+def z_observables(L: int):
+    return [(l, Z.copy()) for l in range(L)]
+
+
+def all_zero(L: int):
+    return [np.array([1.0, 0.0], dtype=np.complex128) for _ in range(L)]
+
+
+def neel(L: int):
+    """|0101...> with site 0 in |0>."""
+    return [np.array([1.0, 0.0] if l % 2 == 0 else [0.0, 1.0], dtype=np.complex128) for l in range(L)]
+
+
+def haar_product(L: int, rng: np.random.Generator):
+    """Independent Haar-random single-site states (normalised complex Gaussians)."""
+    out = []
+    for _ in range(L):
+        v = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+        out.append(v / np.linalg.norm(v))
+    return out
+
+
+@dataclass
+class Workload:
+    """One TJM problem plus the run parameters (the paper's initialisation list)."""
+    name: str
+    W: list
+    jumps: list
+    dt: float
+    n_steps: int
+    chi_max: int
+    trunc_eps: float
+    n_traj: int
+    seed: int
+    psi0: list                      # per-site vectors, shared by all trajectories
+    observables: list
+    sample_steps: list
+    psi0_per_traj: list | None = None   # optional [n_traj][L] site vectors
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def L(self):
+        return len(self.W)
+
+    @property
+    def times(self):
+        return [s * self.dt for s in self.sample_steps]
+
+
+def config_small_fp64(n_traj: int = 200) -> Workload:
+    """L=6 XXX chain, J=1, g=0.5, sigma^- and Z at 0.1 on every site, |0..0>, dt=0.1, T=5, chi_max=16."""
+    L, dt, T = 6, 0.1, 5.0
+    n = int(round(T / dt))
+    return Workload('xxx_L6_chi16_fp64', xxx_mpo(L, 1.0, 0.5), noise(L, 0.1, 0.1), dt, n, 16, 1e-10,
+                    n_traj, 0, all_zero(L), z_observables(L), list(range(n + 1)))
+
+
+def config_l30(n_traj: int = 1024) -> Workload:
+    """L=30 XXX chain, Neel start, dt=0.1, T=10, chi_max=32, 1024 trajectories."""
+    L, dt, T = 30, 0.1, 10.0
+    n = int(round(T / dt))
+    return Workload('xxx_L30_chi32', xxx_mpo(L, 1.0, 0.5), noise(L, 0.1, 0.1), dt, n, 32, 1e-10,
+                    n_traj, 0, neel(L), z_observables(L), list(range(n + 1)))
+
+
+def config_l1000(n_traj: int = 256) -> Workload:
+    """L=1000 XXX chain, Neel start, dt=0.1, T=5, chi_max=64, 256 trajectories."""
+    L, dt, T = 1000, 0.1, 5.0
+    n = int(round(T / dt))
+    return Workload('xxx_L1000_chi64', xxx_mpo(L, 1.0, 0.5), noise(L, 0.1, 0.1), dt, n, 64, 1e-10,
+                    n_traj, 0, neel(L), z_observables(L), list(range(n + 1)))
+
+
+def uneven_groups(seed: int = 7, n_groups: int = 32, per_group: int = 128, dt: float = 0.05, T: float = 5.0):
+    """The uneven batch: 27 groups enumerate L x chi_max x gamma, 5 more drawn at random.
+
+    L in {50, 100, 200}, chi_max in {16, 32, 64}, gamma in {0.01, 0.1, 1.0}
+    (relaxation and dephasing at the same rate), g ~ U[0, 1] per group, and a
+    Haar-random product initial state per trajectory.
+    """
+    rng = np.random.default_rng(seed)
+    grid = [(L, c, g) for L in (50, 100, 200) for c in (16, 32, 64) for g in (0.01, 0.1, 1.0)]
+    params = list(grid)
+    while len(params) < n_groups:
+        params.append((int(rng.choice([50, 100, 200])), int(rng.choice([16, 32, 64])),
+                       float(rng.choice([0.01, 0.1, 1.0]))))
+    n = int(round(T / dt))
+    out = []
+    for gi, (L, chi, gam) in enumerate(params[:n_groups]):
+        gfield = float(rng.uniform(0.0, 1.0))
+        psis = [haar_product(L, rng) for _ in range(per_group)]
+        out.append(Workload(f'group{gi}_L{L}_chi{chi}_g{gam}', xxx_mpo(L, 1.0, gfield), noise(L, gam, gam),
+                            dt, n, chi, 1e-10, per_group, seed, psis[0], z_observables(L), [n],
+                            psi0_per_traj=psis, meta={'g': gfield, 'gamma': gam, 'first_traj': gi * per_group}))
+    return out
+
+
+def request_stream(seed: int = 11, n_requests: int = 200, rate: float = 20.0):
+    """Poisson request arrivals for the serving loop.
+
+    Each request: L ~ U{20..500}, gamma log-uniform in [0.01, 1], g ~ U[0, 1],
+    chi_max in {16, 32, 64}, N ~ U{100..2000}, T ~ U[1, 10], dt = 0.1.
+    Returns [(arrival_time_s, Workload)].
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        L = int(rng.integers(20, 501))
+        gam = float(math.exp(rng.uniform(math.log(0.01), math.log(1.0))))
+        gfield = float(rng.uniform(0.0, 1.0))
+        chi = int(rng.choice([16, 32, 64]))
+        N = int(rng.integers(100, 2001))
+        T = float(rng.uniform(1.0, 10.0))
+        dt = 0.1
+        n = max(1, int(round(T / dt)))
+        out.append((t, Workload(f'req{r}', xxx_mpo(L, 1.0, gfield), noise(L, gam, gam), dt, n, chi, 1e-10,
+                                N, seed * 1000003 + r, neel(L), z_observables(L), [n])))
+    return out
