@@ -1,0 +1,242 @@
+/*
+ * tjm.h -- C ABI of the batched tensor-jump-method library for GB300 (sm_103a).
+ *
+ * The library simulates Lindblad dynamics (arXiv:2501.17913, Eq. Lindblad)
+ * by many independent Monte-Carlo wave-function trajectories, each held as a
+ * matrix product state and advanced by the tensor jump method (TJM): the
+ * dissipative contraction D (Sec. "Dissipative contraction"), the stochastic
+ * jump process J (Sec. "Stochastic jump process") and the dynamic one-/two-
+ * site TDVP U (Sec. "Dynamic TDVP"), in the Strang order of Eq.
+ * TimeEvolutionFunctions with the sampling MPS of Eq. SimulationStep.  All
+ * trajectories of a run advance together on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved (re, im) pairs of doubles, row-major.
+ *   - Physical dimension d = 2 (spin-1/2 chains); other d give TJM_EINVAL.
+ *   - All pointers are HOST pointers.  Inputs are copied during the call; the
+ *     caller keeps ownership of every buffer it passes.  The library owns all
+ *     device memory and releases it in tjm_run_free / tjm_destroy.
+ *   - Every call returns a tjm_status and never aborts the process; the text
+ *     of the last error of a context is available from tjm_last_error.
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef TJM_H
+#define TJM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tjm_ctx tjm_ctx;
+typedef int tjm_status;
+
+enum {
+  TJM_OK = 0,
+  TJM_EINVAL = 1,     /* invalid argument (sizes, shapes, times off the dt grid, ...) */
+  TJM_ENOMEM = 2,     /* device memory exhausted */
+  TJM_ENUMERIC = 3,   /* at least one trajectory hit a non-finite or zero norm */
+  TJM_ETIMEOUT = 4,   /* a bounded device wait gave up */
+  TJM_EBUSY = 5,      /* the run is still executing (tjm_poll) */
+  TJM_EINTERNAL = 6,  /* library bug or inconsistent state */
+  TJM_ECUDA = 7       /* a CUDA runtime call failed; see tjm_last_error */
+};
+
+/* Arithmetic of the GPU path.  FP64: everything in double (the plain FP64
+ * baseline).  FP32: tensor contractions and Krylov vectors in complex FP32
+ * with FP32 accumulation; QR/SVD in FP64; norms, jump weights, Lanczos
+ * coefficients and expectation values accumulated in FP64.  FP32_DEC32: as
+ * FP32 but the QR/SVD factorizations also in FP32 (FP64 accumulations kept). */
+enum { TJM_PREC_FP64 = 0, TJM_PREC_FP32 = 1, TJM_PREC_FP32_DEC32 = 2 };
+
+/* Hamiltonian H0 as a matrix product operator (Methods, Sec. "Matrix product
+ * (density) operators"; Sec. "Initialization" item 2).  D[0..L] are the MPO
+ * bond dimensions with D[0] = D[L] = 1, D[b] <= 8.  W packs the site tensors
+ * one after the other; site l is [D[l]][D[l+1]][d][d] with the first physical
+ * index the output (bra) index:  H0 = sum prod_l W_l[w_l][w_{l+1}][t_l][s_l] |t><s|. */
+typedef struct {
+  int L;
+  int d;
+  const int* D;
+  const double* W;
+} tjm_mpo;
+
+/* A single-site jump operator L_m acting on `site` with coupling rate gamma_m
+ * (Eq. Lindblad; Sec. "Initialization" item 3).  op is 2x2, row-major. */
+typedef struct {
+  int site;
+  double rate;
+  double op[8];
+} tjm_jump;
+
+/* A single-site observable O on `site` (Eq. TJMExpVal); the library returns
+ * Re <Psi|O|Psi> per trajectory. */
+typedef struct {
+  int site;
+  double op[8];
+} tjm_observable;
+
+/* Initial state Psi(0) (Sec. "Initialization" item 1). */
+enum { TJM_STATE_ZERO = 0, TJM_STATE_PRODUCT = 1, TJM_STATE_PRODUCT_PER_TRAJ = 2, TJM_STATE_MPS = 3 };
+typedef struct {
+  int kind;
+  /* PRODUCT: [L][d] complex, one state for all trajectories.
+   * PRODUCT_PER_TRAJ: [n_traj][L][d] complex.
+   * MPS: packed site tensors, site l is [chi[l]][d][chi[l+1]] complex. */
+  const double* data;
+  const int* chi;     /* MPS only: bond dimensions [L + 1], chi[0] = chi[L] = 1 */
+} tjm_state;
+
+typedef struct {
+  int precision;        /* TJM_PREC_*; default TJM_PREC_FP32 */
+  int krylov_max;       /* Lanczos iterations per exponential, <= 30; default 30 */
+  double krylov_tol;    /* Lanczos a-posteriori error tolerance; default 1e-12 (FP64) / 1e-7 (FP32) */
+  int exact_full_bond;  /* 1: pad product states to full bond dimension, never truncate */
+  int device;           /* CUDA device ordinal; default 0 */
+  int max_ctas;         /* 0: one resident wave of CTAs; else an upper bound */
+} tjm_options;
+
+/* Fill opts with the defaults above. */
+void tjm_default_options(tjm_options* opts);
+
+/* tjm_create -- define one TJM problem (Sec. "Initialization" items 2-6).
+ *   H        Hamiltonian MPO (L >= 2).
+ *   jumps    n_jumps single-site jump operators with rates >= 0 (may be 0 jumps).
+ *   dt       time step > 0;  chi_max >= 1 maximum bond dimension (<= 64);
+ *   trunc_eps relative discarded weight allowed per SVD truncation (>= 0).
+ *   opts     may be NULL for the defaults.
+ * The dissipators D_l[dt/2], D_l[dt] of Eq. DissipativeMPO and the MPO layouts
+ * used by the kernels are prepared here and copied to the device.
+ * On success *out owns the context; release it with tjm_destroy. */
+tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, int n_jumps, double dt, int chi_max,
+                      double trunc_eps, const tjm_options* opts);
+
+/* tjm_run -- start N = n_traj trajectories with global ids
+ * first_traj .. first_traj + n_traj - 1, from psi0, recording the n_obs
+ * observables at the n_times times (strictly increasing multiples of dt,
+ * including 0 if wanted; T = times[n_times-1] sets n = T/dt steps).
+ * Trajectory i draws its random numbers from Philox4x32-10 with
+ * key = seed and counter = (global id, step, branch), so results do not depend
+ * on how trajectories are batched or sharded.  Asynchronous: returns after the
+ * launch.  *run_id identifies the run for the calls below. */
+tjm_status tjm_run(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                   const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id);
+
+/* tjm_run_prepare -- as tjm_run but launches nothing: allocates and uploads
+ * the run so that tjm_run_advance can move it forward step by step. */
+tjm_status tjm_run_prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                           const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id);
+
+/* tjm_run_advance -- launch one persistent kernel that moves every trajectory
+ * of the run forward by at most max_steps time steps (the first call also
+ * performs the initialisation and F_0).  Asynchronous.
+ * max_steps = -1 applies only U[dt] of the next step; max_steps = -2 then
+ * applies only that step's main-branch D[dt] and J (no sampling layer):
+ * phase-wise stepping for inspecting the sub-steps with tjm_run_get_state. */
+tjm_status tjm_run_advance(tjm_ctx* ctx, int64_t run_id, int max_steps);
+
+/* tjm_run_group_advance -- one persistent kernel over the trajectories of
+ * several runs (possibly of different contexts on the same device), each
+ * moved forward by at most max_steps steps.  Work is ordered by estimated
+ * cost (largest first).  Launched on the stream of ctxs[0]. */
+tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, int n_runs, int max_steps);
+
+/* tjm_poll -- TJM_OK if the run's device work has finished, TJM_EBUSY if not. */
+tjm_status tjm_poll(tjm_ctx* ctx, int64_t run_id);
+
+/* tjm_result -- wait for the run and copy results.
+ *   mean, sem  [n_times][n_obs]: trajectory average and standard error of the
+ *              mean (Eq. TJMExpVal), may be NULL.
+ *   per_traj   [n_traj][n_times][n_obs], may be NULL.
+ * Returns TJM_ENUMERIC (results still copied) if any trajectory failed
+ * numerically; tjm_run_stats reports how many. */
+tjm_status tjm_result(tjm_ctx* ctx, int64_t run_id, double* mean, double* sem, double* per_traj);
+
+typedef struct {
+  int64_t n_traj, steps_done_min, steps_done_max, failed;
+  uint64_t matvec_one_site, matvec_two_site, matvec_bond, env_updates, krylov_capped, jumps;
+  double min_margin_jump, min_margin_pick;   /* closest |u - threshold| over all jump decisions */
+  int64_t final_bond_sum;                    /* sum over trajectories and bonds of the bond dimension */
+  int64_t final_bond_max;
+} tjm_stats;
+
+/* tjm_run_stats -- work counters of a run (waits for the run). */
+tjm_status tjm_run_stats(tjm_ctx* ctx, int64_t run_id, tjm_stats* out);
+
+/* tjm_run_margins -- per-trajectory smallest distance between a uniform and
+ * its decision threshold (jump / pick), [n_traj] each; may be NULL. */
+tjm_status tjm_run_margins(tjm_ctx* ctx, int64_t run_id, double* margin_jump, double* margin_pick);
+
+/* tjm_run_bonds -- current bond dimensions of every trajectory of the run,
+ * [n_traj][L + 1] ints (waits for the run). */
+tjm_status tjm_run_bonds(tjm_ctx* ctx, int64_t run_id, int* chi);
+
+/* tjm_run_get_state -- copy trajectory `traj` (0-based within the run) of a
+ * run: its completed step count, bond dimensions chi [L + 1] and site tensors
+ * packed as in tjm_state (site l is [chi[l]][d][chi[l+1]] complex; data must
+ * hold sum_l chi[l]*d*chi[l+1] complex numbers, at most L*d*64*64).  The
+ * state is the sampling MPS Phi_j after step j (Sec. "Algorithm"). */
+tjm_status tjm_run_get_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int* step, int* chi, double* data);
+
+/* tjm_run_set_state -- overwrite trajectory `traj` of a run with an MPS in
+ * the layout of tjm_run_get_state and mark it as having completed `step`
+ * steps (checkpoint / resume).  The next advance brings the state to
+ * right-canonical form, normalises it and rebuilds its environments; random
+ * numbers continue from step + 1, so a resumed run reproduces the
+ * uninterrupted one. */
+tjm_status tjm_run_set_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int step, const int* chi,
+                             const double* data);
+
+/* tjm_run_status -- per-trajectory status, [n_traj] (TJM_OK or TJM_ENUMERIC;
+ * a failed trajectory stops advancing and keeps its last good outputs). */
+tjm_status tjm_run_status(tjm_ctx* ctx, int64_t run_id, int* status);
+
+/* tjm_run_free -- release the device memory of a run. */
+tjm_status tjm_run_free(tjm_ctx* ctx, int64_t run_id);
+
+/* The CUDA stream (cudaStream_t) all work of this context is issued on. */
+void* tjm_stream(tjm_ctx* ctx);
+
+/* Block the host until all work of the context has finished. */
+tjm_status tjm_sync(tjm_ctx* ctx);
+
+void tjm_destroy(tjm_ctx* ctx);
+const char* tjm_last_error(const tjm_ctx* ctx);
+
+/* Number of kernels launched so far by this context (for launch accounting). */
+int64_t tjm_launch_count(const tjm_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level self tests: one CTA runs one building block of the trajectory
+ * kernel on one small problem.  Matrices are row-major complex interleaved;
+ * double_precision selects the FP64 (1) or FP32 (0) instantiation.  They
+ * allocate their own device memory and synchronise the device.
+ * ---------------------------------------------------------------------- */
+
+/* Householder QR of A (m x n, m, n <= 256): Q (m x k) with orthonormal
+ * columns, R (k x n) upper triangular, A = Q R, k = min(m, n).  Moves the
+ * MPS orthogonality centre (Methods, Sec. "Matrix product states"). */
+tjm_status tjm_selftest_qr(int double_precision, int m, int n, const double* A, double* Q, double* R);
+
+/* One-sided Jacobi SVD of A (m x n): U (m x nn), S (nn, descending),
+ * V (n x nn), A = U diag(S) V^H, nn = min(m, n); columns of U belonging to
+ * exactly-zero singular values are completed to an orthonormal set.  Used for
+ * the truncations of Sec. "1TDVP and 2TDVP as tensor networks". */
+tjm_status tjm_selftest_svd(int double_precision, int m, int n, const double* A, double* U, double* S, double* V);
+
+/* exp(i theta T) e_1 for the k x k (k <= 32) real symmetric tridiagonal
+ * T = tridiag(beta, alpha, beta): the Lanczos exponential's small factor
+ * (Sec. "1TDVP and 2TDVP as tensor networks", Lanczos method).  c: k complex. */
+tjm_status tjm_selftest_expm_tridiag(int k, const double* alpha, const double* beta, double theta, double* c);
+
+/* The (u1, u2) pair of the Philox4x32-10 stream for n (trajectory, step,
+ * branch) triples under one seed -- the uniforms epsilon of Sec. "Stochastic
+ * jump process" exactly as the trajectory kernel draws them. */
+tjm_status tjm_selftest_philox(uint64_t seed, const uint64_t* traj, const uint32_t* step, const uint32_t* branch, int n,
+                               double* u1, double* u2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TJM_H */

@@ -95,7 +95,7 @@ def rq_move_left(mps, l):
     return C
 
 
-def trunc_rank(S, prob: Problem) -> int:
+def trunc_rank(S, prob: Problem, rec=None) -> int:
     """Number of singular values kept after a two-site update or a jump.
 
     Reading of the paper's "some threshold" (Sec. 1TDVP and 2TDVP as tensor
@@ -117,7 +117,19 @@ def trunc_rank(S, prob: Problem) -> int:
             r = i
         else:
             break
-    return max(1, min(r, prob.chi_max))
+    r = max(1, min(r, prob.chi_max))
+    if rec is not None and n > 1:
+        # how close this decision was to going the other way (diagnostics only):
+        # the discarded tail against the threshold on both sides of the cut
+        thr = prob.trunc_eps * total
+        kept_tail = float(np.sum(w[r:]))
+        m = abs(thr - kept_tail) / total
+        if r - 1 >= 1:
+            m = min(m, abs(kept_tail + w[r - 1] - thr) / total)
+        rec['trunc_margin'] = min(rec.get('trunc_margin', math.inf), m)
+        if r < n:
+            rec['cut_gap'] = min(rec.get('cut_gap', math.inf), float((S[r - 1] - S[r]) / S[0]))
+    return r
 
 
 def local_expectations(mps, ops):
@@ -261,6 +273,7 @@ class Sweeper:
         self.Renv[L] = one
         self.matvecs = {'heff1': 0, 'heff2': 0, 'heff0': 0, 'env': 0}
         self.updates = {'one_site': 0, 'two_site': 0}
+        self.rec = {}
 
     def build_right_envs(self, mps):
         """Renv[b] for b = L-1..1 from a right-canonical MPS (centre at site 0)."""
@@ -299,7 +312,7 @@ class Sweeper:
                 th = np.einsum('asb,bpc->aspc', mps[l], mps[l + 1])
                 th = self._exp('heff2', lambda x, l=l: heff2(Le[l], W[l], W[l + 1], Re[l + 2], x), th, mi)
                 U, S, Vh = np.linalg.svd(th.reshape(chl * d, d * chr_), full_matrices=False)
-                r = trunc_rank(S, p)
+                r = trunc_rank(S, p, self.rec)
                 mps[l] = U[:, :r].reshape(chl, d, r)
                 mps[l + 1] = (S[:r, None] * Vh[:r]).reshape(r, d, chr_)
                 Le[l + 1] = env_left_update(Le[l], mps[l], W[l])
@@ -333,7 +346,7 @@ class Sweeper:
                 th = np.einsum('asb,bpc->aspc', mps[l - 1], mps[l])
                 th = self._exp('heff2', lambda x, l=l: heff2(Le[l - 1], W[l - 1], W[l], Re[l + 1], x), th, mi)
                 U, S, Vh = np.linalg.svd(th.reshape(chl * d, d * chr_), full_matrices=False)
-                r = trunc_rank(S, p)
+                r = trunc_rank(S, p, self.rec)
                 mps[l] = Vh[:r].reshape(r, d, chr_)
                 mps[l - 1] = (U[:, :r] * S[None, :r]).reshape(chl, d, r)
                 Re[l] = env_right_update(Re[l + 1], mps[l], W[l])
@@ -364,7 +377,7 @@ class Sweeper:
 # dissipative contraction D[tau] and stochastic jump J_eps
 # (Sec. "Dissipative contraction", Sec. "Stochastic jump process")
 # --------------------------------------------------------------------------
-def dissipate_and_jump(mps, prob: Problem, Dops, u1, u2):
+def dissipate_and_jump(mps, prob: Problem, Dops, u1, u2, trec=None):
     """Phi <- J_eps( D[tau] Phi ), in place.  Returns a record of the decisions.
 
     Readings:
@@ -418,7 +431,7 @@ def dissipate_and_jump(mps, prob: Problem, Dops, u1, u2):
     for l in range(L - 1, 0, -1):
         chl, d, chr_ = mps[l].shape
         U, S, Vh = np.linalg.svd(mps[l].reshape(chl, d * chr_), full_matrices=False)
-        r = trunc_rank(S, prob)
+        r = trunc_rank(S, prob, trec)
         mps[l] = Vh[:r].reshape(r, d, chr_)
         mps[l - 1] = np.einsum('asb,bk->ask', mps[l - 1], U[:, :r] * S[None, :r])
     mps[0] = mps[0] / np.linalg.norm(mps[0])
@@ -494,26 +507,28 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
             stats['jumps'] += 1
             stats['min_margin2'] = min(stats['min_margin2'], rec['margin2'])
 
+    sw = Sweeper(prob)
     if 0 in want:
         vals[0] = measure(mps, observables)
-    sw = Sweeper(prob)
     if n_steps > 0:
         u1, u2 = uniforms(seed, traj_id, 0, 0)
-        note(dissipate_and_jump(mps, prob, D_half, u1, u2))
+        note(dissipate_and_jump(mps, prob, D_half, u1, u2, sw.rec))
     for j in range(1, n_steps + 1):
         sw.build_right_envs(mps)
         sw.sweep(mps, 0.5 * prob.dt)
         if j in want:
             X = [m.copy() for m in mps]
             u1, u2 = uniforms(seed, traj_id, j, 1)
-            note(dissipate_and_jump(X, prob, D_half, u1, u2))
+            note(dissipate_and_jump(X, prob, D_half, u1, u2, sw.rec))
             vals[j] = measure(X, observables)
         if j < n_steps:
             u1, u2 = uniforms(seed, traj_id, j, 0)
-            note(dissipate_and_jump(mps, prob, D_full, u1, u2))
+            note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec))
     stats['matvecs'] = dict(sw.matvecs)
     stats['updates'] = dict(sw.updates)
     stats['final_bonds'] = [m.shape[2] for m in mps[:-1]]
+    stats['trunc_margin'] = sw.rec.get('trunc_margin', math.inf)
+    stats['cut_gap'] = sw.rec.get('cut_gap', math.inf)
     out = np.array([vals[s] for s in sample_steps]) if sample_steps else np.zeros((0, len(observables)))
     return out, stats
 

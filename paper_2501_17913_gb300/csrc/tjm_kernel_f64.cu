@@ -1,0 +1,24 @@
+// Instantiation of the persistent trajectory kernel: contractions in double,
+// factorizations in double.
+#include "tjm_kernels.cuh"
+#include "tjm_launch.h"
+
+namespace tjm {
+
+cudaError_t launch_f64(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
+                      char* scratch, long long stride, ScratchDims dims) {
+  auto kern = advance_kernel<double, double>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<ctas, TJM_THREADS, kSmemBytes, s>>>(order, n, next, max_steps, scratch, stride, dims);
+  return cudaGetLastError();
+}
+
+int occupancy_f64() {
+  int per_sm = 0;
+  cudaFuncSetAttribute(advance_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<double, double>, TJM_THREADS, kSmemBytes);
+  return per_sm;
+}
+
+}  // namespace tjm

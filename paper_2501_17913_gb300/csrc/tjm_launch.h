@@ -1,0 +1,20 @@
+// Launchers of the persistent trajectory kernel, one per precision pair; each
+// lives in its own translation unit so the three instantiations compile in
+// parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tjm_types.h"
+
+namespace tjm {
+
+#define TJM_DECLARE_LAUNCH(NAME)                                                                              \
+  cudaError_t launch_##NAME(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas, \
+                            char* scratch, long long stride, ScratchDims dims);                               \
+  int occupancy_##NAME();
+
+TJM_DECLARE_LAUNCH(f64)
+TJM_DECLARE_LAUNCH(f32)
+TJM_DECLARE_LAUNCH(f32d32)
+
+}  // namespace tjm

@@ -1,0 +1,296 @@
+// CTA-wide dense factorizations used by the sweeps, in the decomposition
+// precision Td (double in the FP64 path, float or double in the FP32 path):
+//   * Householder QR with explicit thin Q  (moving the orthogonality centre,
+//     Methods Sec. "Matrix product states"; Eq. 1TDVP_ForwardEvolving's QR),
+//   * one-sided (Hestenes) Jacobi SVD       (two-site truncation, post-jump
+//     compression; Sec. "1TDVP and 2TDVP as tensor networks"),
+//   * exp(i theta T) e_1 for the Lanczos tridiagonal T by a scaled Taylor
+//     series on one warp (Moler & Van Loan, "Nineteen dubious ways...", the
+//     series method with scaling), with a Gershgorin-centred shift.
+// Matrices live in global (L2-resident) per-CTA workspace, column-major.
+#pragma once
+#include "tjm_common.cuh"
+
+namespace tjm {
+
+template <class T> struct eps_of;
+template <> struct eps_of<float> { static constexpr double v = 1.1920928955078125e-07; };
+template <> struct eps_of<double> { static constexpr double v = 2.220446049250313e-16; };
+
+// ------------------------------------------------------------------ QR
+// a: m x n column-major (lda = m), factorised in place.  k = min(m, n).
+// On exit q (m x k, column-major) holds the thin Q, r (k x n, column-major,
+// ldr = k) holds R.  tau / rdiag: k entries of scratch each.
+template <class T>
+__device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, cx<T>* rdiag, T* tau, double* red) {
+  const int k = m < n ? m : n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // A remaining column below eps * ||A||_F is rounding noise: no reflector is
+  // built from it (its 1/(v^H v) would overflow in FP32) and it is left as is,
+  // a backward error of at most eps * ||A||_F.
+  double fro2 = 0.0;
+  for (long long e = threadIdx.x; e < (long long)m * n; e += TJM_THREADS) fro2 += (double)norm2(a[e]);
+  fro2 = blk_sum(fro2, red);
+  const double negl = eps_of<T>::v * eps_of<T>::v * fro2;
+  for (int j = 0; j < k; ++j) {
+    cx<T>* col = a + (long long)j * m;
+    double s2 = 0.0;
+    for (int i = j + threadIdx.x; i < m; i += TJM_THREADS) s2 += (double)norm2(col[i]);
+    s2 = blk_sum(s2, red);
+    if (threadIdx.x == 0) {
+      const cx<T> al = col[j];
+      const double sig = sqrt(s2);
+      if (s2 <= negl) {
+        tau[j] = (T)0; rdiag[j] = al;
+      } else {
+        const double aa = sqrt((double)norm2(al));
+        const double px = aa > 0 ? (double)al.x / aa : 1.0, py = aa > 0 ? (double)al.y / aa : 0.0;
+        const cx<T> be = mk((T)(-px * sig), (T)(-py * sig));
+        col[j] = al - be;
+        tau[j] = (T)(1.0 / (s2 + aa * sig));          // 2 / (v^H v)
+        rdiag[j] = be;
+      }
+    }
+    __syncthreads();
+    const T tj = tau[j];
+    if (tj != (T)0) {
+      for (int c = j + 1 + warp; c < n; c += TJM_WARPS) {
+        cx<T>* cc = a + (long long)c * m;
+        cx<T> s = czero<T>();
+        for (int i = j + lane; i < m; i += 32) cfma_cj(s, col[i], cc[i]);
+        s.x = warp_sum(s.x); s.y = warp_sum(s.y);
+        const cx<T> f = mk(-tj * s.x, -tj * s.y);
+        for (int i = j + lane; i < m; i += 32) cfma(cc[i], f, col[i]);
+      }
+    }
+    __syncthreads();
+  }
+  // R (k x n)
+  for (int e = threadIdx.x; e < k * n; e += TJM_THREADS) {
+    const int i = e % k, c = e / k;
+    cx<T> v = czero<T>();
+    if (c > i) v = a[(long long)c * m + i];
+    else if (c == i) v = rdiag[i];
+    r[(long long)c * k + i] = v;
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0]
+  for (int e = threadIdx.x; e < m * k; e += TJM_THREADS) {
+    const int i = e % m, c = e / m;
+    q[e] = (i == c) ? mk((T)1, (T)0) : czero<T>();
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj != (T)0) {
+      const cx<T>* v = a + (long long)j * m;
+      for (int c = j + warp; c < k; c += TJM_WARPS) {
+        cx<T>* qc = q + (long long)c * m;
+        cx<T> s = czero<T>();
+        for (int i = j + lane; i < m; i += 32) cfma_cj(s, v[i], qc[i]);
+        s.x = warp_sum(s.x); s.y = warp_sum(s.y);
+        const cx<T> f = mk(-tj * s.x, -tj * s.y);
+        for (int i = j + lane; i < m; i += 32) cfma(qc[i], f, v[i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi SVD
+// a: mm x nn column-major with mm >= nn (the caller transposes when needed).
+// On exit: u (mm x nn) orthonormal columns sorted by decreasing singular
+// value, s[nn], v (nn x nn) with a = u diag(s) v^H.  Columns of u that belong
+// to exactly-zero singular values are completed to an orthonormal set.
+// work: nn x nn + 3 nn entries of T; iw: 2 nn ints.  Returns the sweep count.
+template <class T>
+__device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T* s, cx<T>* v, cx<T>* vw, int* iw,
+                                           double* red, bool complete) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int rot_count;
+  for (int e = threadIdx.x; e < nn * nn; e += TJM_THREADS) vw[e] = (e % nn == e / nn) ? mk((T)1, (T)0) : czero<T>();
+  const T tol = (T)(eps_of<T>::v * (double)mm);
+  // Columns whose norm falls below eps * ||A||_F carry only rounding noise.
+  // They are set to exactly zero and take no further part in rotations:
+  // otherwise every sweep re-orthogonalises them, shrinks them by another
+  // factor eps and eventually drives them into the denormal range, where the
+  // rotation phases stop being unitary.
+  double fro2 = 0.0;
+  for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) fro2 += (double)norm2(a[e]);
+  fro2 = blk_sum(fro2, red);
+  const T negl = (T)(eps_of<T>::v * eps_of<T>::v * fro2);
+  const int ne = nn + (nn & 1);
+  int sweep = 0;
+  for (; sweep < 40 && nn > 1; ++sweep) {
+    if (threadIdx.x == 0) rot_count = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < ne - 1; ++rnd) {
+      for (int pr = warp; pr < ne / 2; pr += TJM_WARPS) {
+        // circle-method pairing: position 0 fixed, the others rotate
+        const int pa = pr, pb = ne - 1 - pr;
+        const int p = pa == 0 ? 0 : ((pa - 1 + rnd) % (ne - 1)) + 1;
+        const int qq = ((pb - 1 + rnd) % (ne - 1)) + 1;
+        if (p >= nn || qq >= nn) continue;
+        cx<T>* ap = a + (long long)p * mm;
+        cx<T>* aq = a + (long long)qq * mm;
+        T al = 0, be = 0;
+        cx<T> ga = czero<T>();
+        for (int i = lane; i < mm; i += 32) {
+          const cx<T> x = ap[i], y = aq[i];
+          al += norm2(x); be += norm2(y); cfma_cj(ga, x, y);
+        }
+        al = warp_sum(al); be = warp_sum(be); ga.x = warp_sum(ga.x); ga.y = warp_sum(ga.y);
+        if (al <= negl || be <= negl) {
+          if (al <= negl && al != (T)0) for (int i = lane; i < mm; i += 32) ap[i] = czero<T>();
+          if (be <= negl && be != (T)0) for (int i = lane; i < mm; i += 32) aq[i] = czero<T>();
+          continue;
+        }
+        const T ag = sqrt(norm2(ga));
+        if (!(ag > tol * sqrt(al * be))) continue;
+        const T zeta = (be - al) / ((T)2 * ag);
+        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+        const T c = (T)1 / sqrt((T)1 + t * t), sn = c * t;
+        const cx<T> ph = mk(ga.x / ag, -ga.y / ag);           // e^{-i phi}
+        // [a_p, a_q] <- [a_p, a_q] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]
+        for (int i = lane; i < mm; i += 32) {
+          const cx<T> x = ap[i], y = ph * aq[i];
+          ap[i] = c * x - sn * y;
+          aq[i] = sn * x + c * y;
+        }
+        cx<T>* vp = vw + (long long)p * nn;
+        cx<T>* vq = vw + (long long)qq * nn;
+        for (int i = lane; i < nn; i += 32) {
+          const cx<T> x = vp[i], y = ph * vq[i];
+          vp[i] = c * x - sn * y;
+          vq[i] = sn * x + c * y;
+        }
+        if (lane == 0) atomicAdd(&rot_count, 1);
+      }
+      __syncthreads();
+    }
+    const int rc = rot_count;
+    __syncthreads();
+    if (rc == 0) break;
+  }
+  // singular values, descending order (ties by index)
+  T* sv = reinterpret_cast<T*>(vw + (long long)nn * nn);
+  for (int c = warp; c < nn; c += TJM_WARPS) {
+    const cx<T>* ac = a + (long long)c * mm;
+    double acc = 0.0;
+    for (int i = lane; i < mm; i += 32) acc += (double)norm2(ac[i]);
+    acc = warp_sum(acc);
+    if (lane == 0) sv[c] = (T)sqrt(acc);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nn; c += TJM_THREADS) {
+    int rank = 0;
+    const T x = sv[c];
+    for (int i = 0; i < nn; ++i) rank += (sv[i] > x) || (sv[i] == x && i < c);
+    iw[rank] = c;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nn; e += TJM_THREADS) s[e] = sv[iw[e]];
+  for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) {
+    const int i = (int)(e % mm), c = (int)(e / mm);
+    const T sc = sv[iw[c]];
+    const cx<T> x = a[(long long)iw[c] * mm + i];
+    u[e] = sc > (T)0 ? mk(x.x / sc, x.y / sc) : czero<T>();
+  }
+  for (long long e = threadIdx.x; e < (long long)nn * nn; e += TJM_THREADS) {
+    const int i = (int)(e % nn), c = (int)(e / nn);
+    v[e] = vw[(long long)iw[c] * nn + i];
+  }
+  __syncthreads();
+  // complete columns of exactly-zero singular values (Gram-Schmidt on unit
+  // vectors e_cand, scanned cyclically; the residuals of all mm candidates sum
+  // to the dimension still free, so one of them exceeds 1/mm and the
+  // threshold 0.5/mm is always met)
+  if (!complete) return sweep;
+  int cand = 0;
+  const double accept = 0.5 / mm;
+  for (int c = 0; c < nn; ++c) {
+    if (s[c] > (T)0) continue;
+    cx<T>* uc = u + (long long)c * mm;
+    for (int tries = 0; tries < mm; ++tries, cand = (cand + 1) % mm) {
+      for (int i = threadIdx.x; i < mm; i += TJM_THREADS) uc[i] = (i == cand) ? mk((T)1, (T)0) : czero<T>();
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int o = 0; o < nn; ++o) {
+          if (o == c || (s[o] == (T)0 && o > c)) continue;
+          const cx<T>* uo = u + (long long)o * mm;
+          double hx = 0.0, hy = 0.0;
+          for (int i = threadIdx.x; i < mm; i += TJM_THREADS) {
+            const cx<T> x = uo[i], y = uc[i];
+            hx += (double)x.x * y.x + (double)x.y * y.y;
+            hy += (double)x.x * y.y - (double)x.y * y.x;
+          }
+          hx = blk_sum(hx, red);
+          hy = blk_sum(hy, red);
+          for (int i = threadIdx.x; i < mm; i += TJM_THREADS) {
+            const cx<T> x = uo[i];
+            uc[i] = uc[i] - mk((T)(hx * x.x - hy * x.y), (T)(hx * x.y + hy * x.x));
+          }
+          __syncthreads();
+        }
+      }
+      double n2 = 0.0;
+      for (int i = threadIdx.x; i < mm; i += TJM_THREADS) n2 += (double)norm2(uc[i]);
+      n2 = blk_sum(n2, red);
+      if (n2 > accept) {
+        const T f = (T)(1.0 / sqrt(n2));
+        for (int i = threadIdx.x; i < mm; i += TJM_THREADS) uc[i] = f * uc[i];
+        __syncthreads();
+        cand = (cand + 1) % mm;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// ------------------------------------------------------------------ exp of the Lanczos tridiagonal
+// Called by ONE full warp.  c[0..k-1] = exp(i theta T) e_1 with
+// T = tridiag(beta; alpha; beta), k <= 32.  Lane j holds component j.
+__device__ inline void warp_expm_tridiag(int k, const double* alpha, const double* beta, double theta,
+                                         cx<double>* c) {
+  const int j = threadIdx.x & 31;
+  const bool on = j < k;
+  double aj = on ? alpha[j] : 0.0;
+  double amax = on ? aj : -1e300, amin = on ? aj : 1e300;
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    amin = fmin(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+  }
+  const double sh = 0.5 * (amax + amin);
+  const double bj = (on && j + 1 < k) ? beta[j] : 0.0;          // coupling j <-> j+1
+  const double bm = __shfl_up_sync(0xffffffffu, bj, 1);
+  const double bjm = (j > 0 && on) ? bm : 0.0;                  // coupling j-1 <-> j
+  const double ad = on ? aj - sh : 0.0;
+  const double rho = warp_max(on ? fabs(ad) + fabs(bj) + fabs(bjm) : 0.0);
+  int nsc = (int)ceil(fabs(theta) * rho / 0.5);
+  if (nsc < 1) nsc = 1;
+  const double h = theta / nsc;
+  double xr = (j == 0) ? 1.0 : 0.0, xi = 0.0;
+  for (int st = 0; st < nsc; ++st) {
+    double sr = xr, si = xi, tr = xr, ti = xi;
+    for (int n = 1; n <= 16; ++n) {
+      // t <- (i h / n) (T - sh) t
+      const double ur = __shfl_down_sync(0xffffffffu, tr, 1), ui = __shfl_down_sync(0xffffffffu, ti, 1);
+      const double lr = __shfl_up_sync(0xffffffffu, tr, 1), li = __shfl_up_sync(0xffffffffu, ti, 1);
+      double yr = ad * tr + bj * ur + bjm * lr;
+      double yi = ad * ti + bj * ui + bjm * li;
+      if (!on) { yr = 0.0; yi = 0.0; }
+      const double f = h / n;
+      tr = -f * yi;
+      ti = f * yr;
+      sr += tr; si += ti;
+    }
+    xr = sr; xi = si;
+  }
+  // multiply by exp(i theta sh)
+  double cs, sn;
+  sincos(theta * sh, &sn, &cs);
+  if (on) c[j] = mk(cs * xr - sn * xi, cs * xi + sn * xr);
+}
+
+}  // namespace tjm

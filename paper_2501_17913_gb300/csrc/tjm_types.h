@@ -1,0 +1,61 @@
+// Device-side descriptors shared by the host runtime and the kernels.
+// Plain C layout: every pointer is a device pointer.
+#pragma once
+#include <stdint.h>
+
+namespace tjm {
+
+template <class T> struct cx;
+
+// One problem: H as an MPO, the jump operators, dt, chi_max, truncation,
+// observables and the output schedule (TJM Sec. "Initialization").
+struct ProbDev {
+  int L, chi_max, exact, krylov_max;
+  int n_jumps, n_obs, n_steps, n_samples;
+  double dt, trunc_eps, krylov_tol;
+  const int* Dbond;                       // [L + 1] MPO bond dimensions
+  const cx<double>* Wm1; const long long* Wm1_off;   // per site: [(t v)][(w s)]
+  const cx<double>* WmR; const long long* WmR_off;   // per site: [(w t)][(s v)]
+  const cx<double>* W12; const long long* W12_off;   // per bond l: [(t1 t2 v)][(w s1 s2)]
+  const cx<double>* Dhalf;                // [L][4]  D_l[dt/2]
+  const cx<double>* Dfull;                // [L][4]  D_l[dt]
+  const int* jsite;                       // [n_jumps], site-major order
+  const cx<double>* jop;                  // [n_jumps][4]
+  const cx<double>* jLdL;                 // [n_jumps][4]  L^dag L
+  const double* jgamma;                   // [n_jumps]
+  const int* osite;                       // [n_obs]
+  const cx<double>* oop;                  // [n_obs][4]
+  const int* sample_row;                  // [n_steps + 1] -> output row or -1
+};
+
+struct SlotStats {
+  unsigned long long mv_heff1, mv_heff2, mv_heff0, env_updates, krylov_capped, jumps;
+  double min_margin1, min_margin2;
+};
+
+// One trajectory.
+struct SlotDev {
+  const ProbDev* prob;
+  unsigned long long traj_id, seed;
+  int step;            // -1: not started; j: F_0..F_j done (Phi_j held)
+  int status;          // 0 ok, 3 numeric failure
+  int chi_cap;
+  int flags;           // bit 0: state loaded from outside (canonicalise, rebuild envs)
+                       // bit 1: U[dt] of step+1 applied, X held (phase-wise stepping)
+  void* sites;         // [L][cap_site] complex Tc
+  int* chi;            // [L + 1]
+  void* envL;          // [L + 1][cap_env]
+  void* envR;          // [L + 1][cap_env]
+  long long cap_site, cap_env;
+  double* out;         // [n_samples][n_obs]
+  const cx<double>* init;   // initial MPS, packed site tensors
+  const int* init_chi;      // [L + 1]
+  SlotStats stats;
+};
+
+// Per-CTA scratch sizing (elements); identical arithmetic on host and device.
+struct ScratchDims {
+  int chi_cap, Dmax, kmax, Lmax, jmax;
+};
+
+}  // namespace tjm

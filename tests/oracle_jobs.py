@@ -23,4 +23,5 @@ def run_traj(args):
     samples = [s for s in wl.sample_steps if s <= n_steps]
     v, st = O1.run_trajectory(prob, mps, gid, wl.seed, wl.observables, n_steps, samples)
     return v, {'jumps': st['jumps'], 'min_margin1': st['min_margin1'], 'min_margin2': st['min_margin2'],
-               'matvecs': st['matvecs'], 'updates': st['updates'], 'final_bonds': st['final_bonds']}
+               'matvecs': st['matvecs'], 'updates': st['updates'], 'final_bonds': st['final_bonds'],
+               'trunc_margin': st['trunc_margin'], 'cut_gap': st['cut_gap']}
