@@ -1,0 +1,336 @@
+"""Benchmark: trajectory*site*steps/s of the tensor jump method on GB300.
+
+Workload (one GPU): XXX chain L = 1000, J = 1, g = 0.5, sigma^- and Z noise at
+gamma = 0.1 on every site, dt = 0.1, chi_max = 64, 256 trajectories, <Z_i>
+sampled at every step, started from a seeded random MPS with every bulk bond
+at chi = 64 (the bond-saturated regime the chi = 64 throughput refers to).
+A step is one full TJM time step of every trajectory: U[dt] (dynamic TDVP),
+the sampling layer J'(D[dt/2]) with the observables, and J(D[dt]).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank simulates its own 256 trajectories (global ids
+rank*256 ...), weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trajectory*site*steps/s at L=1000 chi=64"
+UNIT = "trajectory*site*steps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32d64", "fp64"])
+    p.add_argument("--L", type=int, default=1000)
+    p.add_argument("--chi", type=int, default=64)
+    p.add_argument("--ntraj", type=int, default=256)
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 slice")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- the oracle (CPU)
+def _oracle_step_job(args):
+    """One oracle TJM step of one trajectory on an L-site chi-saturated chain; returns seconds."""
+    L, chi, traj, seed = args
+    import numpy as np
+    from oracle import mps_tjm as O1
+    from oracle.philox import uniforms
+    from paper_2501_17913_gb300 import inputs as I
+    W = I.xxx_mpo(L, 1.0, 0.5)
+    prob = O1.Problem(W, I.noise(L, 0.1, 0.1), 0.1, chi, 1e-10)
+    _, sites = I.random_mps(L, chi, seed)
+    mps = [np.array(s) for s in sites]
+    for l in range(L - 1, 0, -1):
+        O1.rq_move_left(mps, l)
+    mps[0] = mps[0] / np.linalg.norm(mps[0])
+    D_half = [O1.dissipator_site(prob, l, 0.05) for l in range(L)]
+    D_full = [O1.dissipator_site(prob, l, 0.1) for l in range(L)]
+    t0 = time.perf_counter()
+    sw = O1.Sweeper(prob)
+    sw.build_right_envs(mps)
+    sw.sweep(mps, 0.05)
+    X = [m.copy() for m in mps]
+    O1.dissipate_and_jump(X, prob, D_half, *uniforms(seed, traj, 1, 1))
+    O1.measure(X, I.z_observables(L))
+    O1.dissipate_and_jump(mps, prob, D_full, *uniforms(seed, traj, 1, 0))
+    return time.perf_counter() - t0
+
+
+def oracle_sample(cores, L=24, chi=64, rounds=1):
+    """Time the oracle on `cores` trajectories at once (one per core), `rounds` steps each."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import multiprocessing as mp
+    jobs = [(L, chi, t, 11) for t in range(cores * rounds)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        per = pool.map(_oracle_step_job, jobs)
+    wall = time.perf_counter() - t0
+    busy = sum(per)
+    # throughput of the busy cores: trajectory*site*steps per second of wall time
+    value = len(jobs) * L / (busy / cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d trajectories x 1 TJM step of an L=%d XXX chain at chi=%d (random chi-saturated MPS, "
+                      "same H, noise, dt), numpy FP64 oracle, one trajectory per core; per-site rate" %
+                      (len(jobs), L, chi),
+            "wall_s": wall, "cpu_s": busy}
+
+
+def run_reference(a):
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(a.warmup):
+        oracle_sample(cores, rounds=1)
+    t0 = time.perf_counter()
+    tot = 0.0
+    for _ in range(a.steps):
+        r = oracle_sample(cores, rounds=1)
+        tot += r["cpu_s"] / cores
+    value = a.steps * cores * 24 / tot
+    ms = 1000.0 * tot / a.steps
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": "xxx_L24_chi64_oracle_sample", "note": "CPU FP64 oracle; per-site rate of "
+                      "one TJM step on a chi=64-saturated chain, one trajectory per core"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d trajectories x 1 step per timed step, L=24, chi=64" % cores},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- ours (GPU)
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_17913_gb300 import build as B
+    from paper_2501_17913_gb300 import inputs as I
+    from paper_2501_17913_gb300 import tjm
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    prec = {"fp32": tjm.PREC_FP32_DEC32, "fp32d64": tjm.PREC_FP32, "fp64": tjm.PREC_FP64}[a.precision]
+    L, chi, N, dt = a.L, a.chi, a.ntraj, 0.1
+    n_total = a.warmup + a.steps
+    W = I.xxx_mpo(L, 1.0, 0.5)
+    jumps = I.noise(L, 0.1, 0.1)
+    obs = I.z_observables(L)
+    psi = I.random_mps(L, chi, 2025)
+    times = [dt * j for j in range(n_total + 1)]
+    ctx = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local)
+    rid = ctx.prepare(psi, N, 0, obs, times, first_traj=rank * N)
+    stream = torch.cuda.ExternalStream(ctx.stream())
+    ctx.advance(rid, 0)                      # initialisation, F_0
+    for _ in range(a.warmup):
+        ctx.advance(rid, 1)
+    ctx.sync()
+    s0 = ctx.stats(rid)
+    launches0 = ctx.launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        ctx.advance(rid, 1)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    s1 = ctx.stats(rid)
+    gpu_launches = (ctx.launches() - launches0) * 2   # each advance: one counter memset + one trajectory kernel
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * N * L * a.steps / (t_max / 1000.0)
+    fc = s1["flops_contract"] - s0["flops_contract"]
+    fd = s1["flops_decomp"] - s0["flops_decomp"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # CUDA-core FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    fp64_peak = n_sm * 2 * 2 * sm_max * 1e6 / 1e12      # FP64 FMA: 2 per SM per clock on GB300
+    achieved = fc / (ms / 1000.0) / 1e12
+    if prec == tjm.PREC_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None}
+    roof["kernel"] = "tjm::advance_kernel"
+    roof["peak_source"] = "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (CUDA-core FMA)" % (n_sm, sm_max) \
+        if prec != tjm.PREC_FP64 else "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, sm_max)
+    roof["achieved_counts"] = "contraction flops counted on device (8 per complex MAC) / CUDA-event time"
+    roof["decomp_tflops"] = fd / (ms / 1000.0) / 1e12
+    extra = {}
+    # end to end through the C ABI with host buffers: tjm_run (init + F_0 + K steps) and tjm_result
+    if not a.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local)
+        times2 = [dt * j for j in range(a.steps + 1)]
+        r2 = ctx2.run(psi, N, 0, obs, times2, first_traj=rank * N)
+        mean, sem, pt = ctx2.result(r2)
+        t_e2e = time.perf_counter() - t0
+        h2d = sum(x.size for x in psi[1]) * 16 + len(psi[0]) * 4
+        d2h = pt.nbytes + mean.nbytes + sem.nbytes
+        e2e = {"value": world * N * L * a.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // a.steps,
+               "d2h_bytes_per_step": d2h // a.steps, "wall_s": t_e2e,
+               "note": "tjm_run from host inputs (init, F_0, K steps) + tjm_result to host"}
+        gpu_launches_e2e = ctx2.launches()
+        ctx2.close()
+    else:
+        e2e = None
+    # plain FP64 GPU path on a slice of the workload (same H, noise, dt, chi; L=100, 1 step)
+    if not a.no_fp64 and rank == 0:
+        L64, N64 = 100, n_sm
+        W64 = I.xxx_mpo(L64, 1.0, 0.5)
+        ctx3 = tjm.Context(W64, I.noise(L64, 0.1, 0.1), dt, chi, 1e-10, precision=tjm.PREC_FP64, device=local)
+        r3 = ctx3.prepare(I.random_mps(L64, chi, 2025), N64, 0, I.z_observables(L64), [dt, 2 * dt])
+        ctx3.advance(r3, 0)
+        ctx3.sync()
+        st3 = torch.cuda.ExternalStream(ctx3.stream())
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(st3)
+        ctx3.advance(r3, 1)
+        f1.record(st3)
+        f1.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        extra["fp64_gpu"] = {"value": N64 * L64 / (ms64 / 1000.0), "unit": UNIT,
+                             "slice": "%d trajectories x 1 step, L=%d, chi=64 (random chi-saturated MPS)" % (N64, L64),
+                             "ms": ms64}
+        ctx3.close()
+    cpu = None
+    if not a.no_cpu and rank == 0:
+        cpu = oracle_sample(max(1, min(os.cpu_count() or 1, 16)))
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None,
+               "dtype": {"fp32": "f32", "fp32d64": "f32+f64", "fp64": "f64"}[a.precision],
+               "data": "synthetic",
+               "config": {"workload": "xxx_L%d_chi%d_N%d_random_chi_saturated" % (L, chi, N), "L": L, "chi_max": chi,
+                          "trajectories_per_gpu": N, "dt": dt, "gamma": 0.1, "g": 0.5,
+                          "precision": a.precision, "l2": "inputs larger than L2 (trajectory state %.1f GB)" %
+                          (N * (L * 2 * chi * chi + 2 * (L + 1) * 5 * chi * chi) * (8 if prec else 16) / 1e9),
+                          "parallelism": "trajectories" + ("x%d" % world if world > 1 else "")},
+               "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
+               "e2e": e2e, "cpu_baseline": cpu,
+               "stats": {"jumps": s1["jumps"] - s0["jumps"],
+                         "matvecs_one_site": s1["matvec_one_site"] - s0["matvec_one_site"],
+                         "matvecs_bond": s1["matvec_bond"] - s0["matvec_bond"],
+                         "matvecs_two_site": s1["matvec_two_site"] - s0["matvec_two_site"],
+                         "contract_gflop": fc / 1e9, "decomp_gflop": fd / 1e9}}
+        if "fp64_gpu" in extra:
+            out["fp64_gpu"] = extra["fp64_gpu"]
+            out["vs_fp64_gpu"] = value / world / extra["fp64_gpu"]["value"]
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

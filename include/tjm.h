@@ -159,6 +159,8 @@ typedef struct {
   double min_margin_jump, min_margin_pick;   /* closest |u - threshold| over all jump decisions */
   int64_t final_bond_sum;                    /* sum over trajectories and bonds of the bond dimension */
   int64_t final_bond_max;
+  double flops_contract;                     /* real flops of all tensor contractions (8 per complex MAC) */
+  double flops_decomp;                       /* real flops of the QR / SVD factorizations */
 } tjm_stats;
 
 /* tjm_run_stats -- work counters of a run (waits for the run). */

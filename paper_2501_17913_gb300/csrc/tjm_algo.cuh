@@ -47,6 +47,16 @@ template <class Tc, class Td> struct Ctx {
   __device__ cx<Tc>* Renv(int b) const { return envR + (long long)b * cap_env; }
 };
 
+// Work counters (thread 0 only; one CTA owns a slot).
+template <class Tc, class Td>
+__device__ __forceinline__ void count_contract(const Ctx<Tc, Td>& c, double cmacs) {
+  if (threadIdx.x == 0) c.S->stats.flops_contract += 8.0 * cmacs;
+}
+template <class Tc, class Td>
+__device__ __forceinline__ void count_decomp(const Ctx<Tc, Td>& c, double cmacs) {
+  if (threadIdx.x == 0) c.S->stats.flops_decomp += 8.0 * cmacs;
+}
+
 // ------------------------------------------------------------------ site-local operator
 // M[a][t][b] <- sum_s op[t][s] M[a][s][b]   (op: 2x2 complex double, row-major)
 template <class Tc>
@@ -80,6 +90,8 @@ __device__ __noinline__ void heff1(const Ctx<Tc, Td>& c, int l, const cx<Tc>* x,
   // G3: y[(x t), y'] = T2[(x t), (v b)] R[(v b), y']
   blk_gemm<Tc>(chl * kD, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 1), chr, 1), y, chr, 1,
                c.gsm);
+  count_contract(c, (double)chl * Dl * kD * chr * chl + (double)chl * chr * kD * Dr * Dl * kD +
+                        (double)chl * kD * chr * Dr * chr);
 }
 
 // Two sites (l, l+1) on theta[a][s1][s2][b]
@@ -92,6 +104,8 @@ __device__ __noinline__ void heff2(const Ctx<Tc, Td>& c, int l, int chl, int chr
                  (long long)d2 * Dr * chr, chr, c.gsm);
   blk_gemm<Tc>(chl * d2, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 2), chr, 1), y, chr, 1,
                c.gsm);
+  count_contract(c, (double)chl * Dl * d2 * chr * chl + (double)chl * chr * d2 * Dr * Dl * d2 +
+                        (double)chl * d2 * chr * Dr * chr);
 }
 
 // Bond b (between sites b-1 and b): y[x][y'] = sum Lenv[b][x,w,a] C[a,b'] Renv[b][w,b',y']
@@ -100,6 +114,7 @@ __device__ __noinline__ void heff0(const Ctx<Tc, Td>& c, int b, int chl, int chr
   const int D = c.P->Dbond[b];
   blk_gemm<Tc>(chl * D, chr, chl, matA(c.Lenv(b), chl, 1), matB(x, chr, 1), c.t1, chr, 1, c.gsm);
   blk_gemm<Tc>(chl, chr, D * chr, matA(c.t1, (long long)D * chr, 1), matB(c.Renv(b), chr, 1), y, chr, 1, c.gsm);
+  count_contract(c, (double)chl * D * chr * chl + (double)chl * chr * D * chr);
 }
 
 // Lenv[l+1][y][v][b] = sum conj(A[x,t,y]) Lenv[l][x,w,a] W[w,v,t,s] A[a,s,b]
@@ -113,6 +128,8 @@ __device__ __noinline__ void env_left(const Ctx<Tc, Td>& c, int l) {
                  (long long)kD * Dr * chr, chr, c.gsm);
   blk_gemm<Tc>(chr, Dr * chr, chl * kD, matA(A, 1, chr, 1), matB(c.t2, (long long)Dr * chr, 1), c.Lenv(l + 1),
                (long long)Dr * chr, 1, c.gsm);
+  count_contract(c, (double)chl * Dl * kD * chr * chl + (double)chl * chr * kD * Dr * Dl * kD +
+                        (double)chr * Dr * chr * chl * kD);
 }
 
 // Renv[l][w][a][x] = sum B[a,s,b] W[w,v,t,s] Renv[l+1][v,b,y] conj(B[x,t,y])
@@ -131,6 +148,8 @@ __device__ __noinline__ void env_right(const Ctx<Tc, Td>& c, int l) {
   // Rnew[w][a][x] = S2[a][w][(t y)] conj(B[x][(t y)])
   blk_gemm_batched<Tc>(Dl, chl, chl, kD * chr, mk((Tc)1, (Tc)0), matA(c.t2, (long long)Dl * kD * chr, 1), kD * chr,
                        matB(B, 1, kD * chr, 1), 0, c.Renv(l), chl, 1, (long long)chl * chl, false, c.gsm);
+  count_contract(c, (double)Dr * chl * kD * chr * chr + (double)chl * chr * Dl * kD * kD * Dr +
+                        (double)Dl * chl * chl * kD * chr);
 }
 
 template <class Tc, class Td>
@@ -260,6 +279,11 @@ __device__ __noinline__ int qr_of(const Ctx<Tc, Td>& c, int rows, int cols, cons
   __syncthreads();
   blk_qr<Td>(rows, cols, c.da, c.du, c.dv, c.drd, c.dtau, c.red);
   __syncthreads();
+  {
+    const double k = rows < cols ? rows : cols;
+    // Householder factorization and explicit thin Q: 2 (m n^2 - n^3/3) complex multiply-adds each way
+    count_decomp(c, 4.0 * ((double)rows * cols * k - k * k * k / 3.0));
+  }
   return rows < cols ? rows : cols;
 }
 
@@ -372,7 +396,9 @@ __device__ __noinline__ int svd_of(const Ctx<Tc, Td>& c, int m, int n, const cx<
   }
   __syncthreads();
   // on the work matrix: Wk = Uw diag(s) Vw^H; Uw -> du (mm x nn), Vw -> dv (nn x nn)
-  blk_svd_jacobi<Td>(mm, nn, c.da, c.du, c.ds, c.dv, c.dvw, c.iw, c.red, c.P->exact != 0);
+  const int sweeps = blk_svd_jacobi<Td>(mm, nn, c.da, c.du, c.ds, c.dv, c.dvw, c.iw, c.red, c.P->exact != 0);
+  // per sweep and pair: three column dot products and two column rotations (A and V)
+  count_decomp(c, (double)(sweeps + 1) * 0.5 * nn * (nn - 1) * (3.0 * mm + 2.0 * (mm + nn)));
   if (tr) {
     // A = (Wk)^H = Vw diag(s) Uw^H : U = Vw (m x nn), V = Uw (n x nn); swap buffers by copy
     for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) c.da[e] = c.du[e];

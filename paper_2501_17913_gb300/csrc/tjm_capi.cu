@@ -781,6 +781,8 @@ tjm_status tjm_run_stats(tjm_ctx* ctx, int64_t run_id, tjm_stats* out) {
     out->jumps += S.stats.jumps;
     out->min_margin_jump = std::min(out->min_margin_jump, S.stats.min_margin1);
     out->min_margin_pick = std::min(out->min_margin_pick, S.stats.min_margin2);
+    out->flops_contract += S.stats.flops_contract;
+    out->flops_decomp += S.stats.flops_decomp;
   }
   std::vector<int> chi((size_t)R->n_traj * (R->L + 1));
   TJM_CU(cudaMemcpy(chi.data(), R->chi, chi.size() * sizeof(int), cudaMemcpyDeviceToHost));

@@ -31,6 +31,8 @@ struct ProbDev {
 struct SlotStats {
   unsigned long long mv_heff1, mv_heff2, mv_heff0, env_updates, krylov_capped, jumps;
   double min_margin1, min_margin2;
+  double flops_contract;   // real flops of the tensor contractions (8 per complex multiply-add)
+  double flops_decomp;     // real flops of the QR / SVD factorizations (Jacobi: per rotation applied)
 };
 
 // One trajectory.

@@ -182,3 +182,22 @@ def request_stream(seed: int = 11, n_requests: int = 200, rate: float = 20.0):
         out.append((t, Workload(f'req{r}', xxx_mpo(L, 1.0, gfield), noise(L, gam, gam), dt, n, chi, 1e-10,
                                 N, seed * 1000003 + r, neel(L), z_observables(L), [n])))
     return out
+
+
+def random_mps(L: int, chi_max: int, seed: int = 1234):
+    """A seeded random MPS with every bond at min(chi_max, 2^b, 2^(L-b)).
+
+    Entries are complex Gaussians of variance 1/(2 chi_right), so the right
+    transfer map sum_s M^s (.) M^s^dag preserves the identity on average and
+    the norm neither overflows nor underflows along a long chain.  Used as a
+    bond-saturated starting point ("chi-saturated regime").
+    Returns (chi [L+1], [site tensors (chi_l, 2, chi_r)]).
+    """
+    rng = np.random.default_rng(seed)
+    chi = [min(chi_max, 2 ** min(b, 30), 2 ** min(L - b, 30)) for b in range(L + 1)]
+    sites = []
+    for l in range(L):
+        a, b = chi[l], chi[l + 1]
+        x = rng.standard_normal((a, 2, b)) + 1j * rng.standard_normal((a, 2, b))
+        sites.append(x / math.sqrt(2.0 * 2 * b))
+    return chi, sites

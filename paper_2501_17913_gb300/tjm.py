@@ -47,7 +47,8 @@ class tjm_stats(C.Structure):
                 ("failed", C.c_int64), ("matvec_one_site", C.c_uint64), ("matvec_two_site", C.c_uint64),
                 ("matvec_bond", C.c_uint64), ("env_updates", C.c_uint64), ("krylov_capped", C.c_uint64),
                 ("jumps", C.c_uint64), ("min_margin_jump", C.c_double), ("min_margin_pick", C.c_double),
-                ("final_bond_sum", C.c_int64), ("final_bond_max", C.c_int64)]
+                ("final_bond_sum", C.c_int64), ("final_bond_max", C.c_int64),
+                ("flops_contract", C.c_double), ("flops_decomp", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
