@@ -238,6 +238,32 @@ tjm_status tjm_selftest_expm_tridiag(int k, const double* alpha, const double* b
 tjm_status tjm_selftest_philox(uint64_t seed, const uint64_t* traj, const uint32_t* step, const uint32_t* branch, int n,
                                double* u1, double* u2);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free SVD (the paper has no counterpart; this is a library
+ * utility).  For callers that cannot let a library allocate device memory:
+ * applications whose own pool or arena allocator owns all device memory, and
+ * latency-sensitive loops that must not pay for cudaMalloc/cudaFree (cudaFree
+ * synchronises the whole device).
+ *
+ * tjm_svd_noalloc -- the same one-CTA Jacobi SVD as tjm_selftest_svd, with
+ * DEVICE pointers: A (m x n), U (m x nn), S (nn), V (n x nn), nn = min(m, n),
+ * row-major complex interleaved doubles (S real), A = U diag(S) V^H, S
+ * descending.  The caller owns and provides all four buffers; the call
+ * allocates nothing.  Its workspace is one static device array of about
+ * 1.1 MB sized for m, n <= TJM_NOALLOC_MAX_DIM, held by every GPU that loads
+ * the library until the process exits; larger m or n return TJM_EINVAL.
+ * The kernel is queued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting.  The first call on each
+ * device looks up the workspace's device address (cudaGetSymbolAddress with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the one workspace and leaves its contents
+ * behind (nothing in it needs clearing): calls whose kernels overlap on the
+ * GPU (different streams without ordering) race and corrupt each other.
+ * Returns TJM_ECUDA if the launch fails. */
+#define TJM_NOALLOC_MAX_DIM 128
+tjm_status tjm_svd_noalloc(int double_precision, int m, int n, const double* A, double* U, double* S, double* V,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif
