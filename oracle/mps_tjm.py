@@ -141,16 +141,16 @@ def local_expectations(mps, ops):
     L = len(mps)
     Lt = [np.ones((1, 1), dtype=np.complex128)]
     for l in range(L):
-        Lt.append(np.einsum('ab,asc,bsd->cd', Lt[l], mps[l].conj(), mps[l]))
+        Lt.append(np.einsum('ab,asc,bsd->cd', Lt[l], mps[l].conj(), mps[l], optimize=True))
     Rt = [None] * (L + 1)
     Rt[L] = np.ones((1, 1), dtype=np.complex128)
     for l in range(L - 1, -1, -1):
-        Rt[l] = np.einsum('asc,bsd,cd->ab', mps[l].conj(), mps[l], Rt[l + 1])
+        Rt[l] = np.einsum('asc,bsd,cd->ab', mps[l].conj(), mps[l], Rt[l + 1], optimize=True)
     norm2 = Lt[L][0, 0].real
     vals = []
     for (site, op) in ops:
         M = mps[site]
-        vals.append(np.einsum('ab,atc,ts,bsd,cd->', Lt[site], M.conj(), op, M, Rt[site + 1]))
+        vals.append(np.einsum('ab,atc,ts,bsd,cd->', Lt[site], M.conj(), op, M, Rt[site + 1], optimize=True))
     return np.array(vals), norm2
 
 
@@ -500,7 +500,8 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
     vals = {}
     stats = {'jumps': 0, 'min_margin1': math.inf, 'min_margin2': math.inf, 'records': []}
 
-    def note(rec):
+    def note(rec, step):
+        rec['step'] = step
         stats['records'].append(rec)
         stats['min_margin1'] = min(stats['min_margin1'], rec['margin1'])
         if rec['jump'] >= 0:
@@ -512,18 +513,18 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
         vals[0] = measure(mps, observables)
     if n_steps > 0:
         u1, u2 = uniforms(seed, traj_id, 0, 0)
-        note(dissipate_and_jump(mps, prob, D_half, u1, u2, sw.rec))
+        note(dissipate_and_jump(mps, prob, D_half, u1, u2, sw.rec), 0)
     for j in range(1, n_steps + 1):
         sw.build_right_envs(mps)
         sw.sweep(mps, 0.5 * prob.dt)
         if j in want:
             X = [m.copy() for m in mps]
             u1, u2 = uniforms(seed, traj_id, j, 1)
-            note(dissipate_and_jump(X, prob, D_half, u1, u2, sw.rec))
+            note(dissipate_and_jump(X, prob, D_half, u1, u2, sw.rec), j)
             vals[j] = measure(X, observables)
         if j < n_steps:
             u1, u2 = uniforms(seed, traj_id, j, 0)
-            note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec))
+            note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec), j)
     stats['matvecs'] = dict(sw.matvecs)
     stats['updates'] = dict(sw.updates)
     stats['final_bonds'] = [m.shape[2] for m in mps[:-1]]
