@@ -95,6 +95,11 @@ typedef struct {
   int exact_full_bond;  /* 1: pad product states to full bond dimension, never truncate */
   int device;           /* CUDA device ordinal; default 0 */
   int max_ctas;         /* 0: one resident wave of CTAs; else an upper bound */
+  int energy_shift;     /* 1 (default): evolve with H - E*I, E the trajectory's energy at the start of
+                         * each step, when H is in finite-state form (identity strings in the first
+                         * and last MPO channels).  A constant shift only changes the global phase,
+                         * so observables are unchanged; it keeps the FP32 environment sums near
+                         * zero instead of near the extensive energy.  0: evolve with H as given. */
 } tjm_options;
 
 /* Fill opts with the defaults above. */
@@ -161,6 +166,10 @@ typedef struct {
   int64_t final_bond_max;
   double flops_contract;                     /* real flops of all tensor contractions (8 per complex MAC) */
   double flops_decomp;                       /* real flops of the QR / SVD factorizations */
+  uint64_t cycles[12];                       /* SM cycles summed over trajectories, by phase: GEMM, MPO
+                                                contraction, Lanczos, QR, SVD, dissipation+jump, measurement,
+                                                TDVP sweep, environment build, Krylov exponential, matvec
+                                                inside Lanczos, initialisation */
 } tjm_stats;
 
 /* tjm_run_stats -- work counters of a run (waits for the run). */

@@ -43,9 +43,29 @@ template <class Tc, class Td> struct Ctx {
   double* wts;           // jump weights
   // shared memory
   char* gsm; double* red; double* sc;
+  char* fsm;             // factorization workspace in shared memory (nullptr if none)
+  int fsm_bytes;         // its size
+  char* fsv;             // shared scratch for unsorted singular values (fsm_bytes > 0 only)
   __device__ cx<Tc>* Lenv(int b) const { return envL + (long long)b * cap_env; }
   __device__ cx<Tc>* Renv(int b) const { return envR + (long long)b * cap_env; }
 };
+
+// Phase timer: every wrapped statement ends in a CTA-wide barrier, so thread
+// 0's clock64() interval is the CTA's time in that phase.
+#define TJM_TIMED(c, ph, stmt)                                                   \
+  do {                                                                           \
+    const long long _t0 = clock64();                                             \
+    stmt;                                                                        \
+    if (threadIdx.x == 0) (c).S->stats.cyc[ph] += (unsigned long long)(clock64() - _t0); \
+  } while (0)
+
+// Energy shift per site: H - eshift * sum_i I_i has its expectation value near
+// zero, so the FP32 sums of the environment contractions stay small.  A
+// constant shift only multiplies every local exponential by a phase.
+template <class Tc, class Td>
+__device__ __forceinline__ double site_shift(const Ctx<Tc, Td>& c) {
+  return c.P->shift_ok ? -c.S->eshift : 0.0;
+}
 
 // Work counters (thread 0 only; one CTA owns a slot).
 template <class Tc, class Td>
@@ -83,13 +103,13 @@ __device__ __noinline__ void heff1(const Ctx<Tc, Td>& c, int l, const cx<Tc>* x,
   const int chl = c.mps.chi[l], chr = c.mps.chi[l + 1];
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 1];
   // G1: T1[(x w), (s b)] = L[(x w), a] M[a, (s b)]
-  blk_gemm<Tc>(chl * Dl, kD * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, kD * chr, 1), c.t1, kD * chr, 1, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, kD * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, kD * chr, 1), c.t1, kD * chr, 1, c.gsm));
   // G2: T2[x][(t v)][b] = sum_(w s) Wm1[(t v)][(w s)] T1[x][(w s)][b]
-  blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
-                 (long long)kD * Dr * chr, chr, c.gsm);
+  TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
+                 (long long)kD * Dr * chr, chr, c.gsm, site_shift(c), kD, Dr - 1, Dr, 0, 1));
   // G3: y[(x t), y'] = T2[(x t), (v b)] R[(v b), y']
-  blk_gemm<Tc>(chl * kD, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 1), chr, 1), y, chr, 1,
-               c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * kD, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 1), chr, 1), y, chr, 1,
+               c.gsm));
   count_contract(c, (double)chl * Dl * kD * chr * chl + (double)chl * chr * kD * Dr * Dl * kD +
                         (double)chl * kD * chr * Dr * chr);
 }
@@ -99,11 +119,11 @@ template <class Tc, class Td>
 __device__ __noinline__ void heff2(const Ctx<Tc, Td>& c, int l, int chl, int chr, const cx<Tc>* x, cx<Tc>* y) {
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 2];
   const int d2 = kD * kD;
-  blk_gemm<Tc>(chl * Dl, d2 * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, d2 * chr, 1), c.t1, d2 * chr, 1, c.gsm);
-  blk_wapply<Tc>(chl, d2 * Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, (long long)Dl * d2 * chr, chr, c.t2,
-                 (long long)d2 * Dr * chr, chr, c.gsm);
-  blk_gemm<Tc>(chl * d2, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 2), chr, 1), y, chr, 1,
-               c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, d2 * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, d2 * chr, 1), c.t1, d2 * chr, 1, c.gsm));
+  TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, d2 * Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, (long long)Dl * d2 * chr, chr, c.t2,
+                 (long long)d2 * Dr * chr, chr, c.gsm, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * d2, chr, Dr * chr, matA(c.t2, (long long)Dr * chr, 1), matB(c.Renv(l + 2), chr, 1), y, chr, 1,
+               c.gsm));
   count_contract(c, (double)chl * Dl * d2 * chr * chl + (double)chl * chr * d2 * Dr * Dl * d2 +
                         (double)chl * d2 * chr * Dr * chr);
 }
@@ -112,8 +132,8 @@ __device__ __noinline__ void heff2(const Ctx<Tc, Td>& c, int l, int chl, int chr
 template <class Tc, class Td>
 __device__ __noinline__ void heff0(const Ctx<Tc, Td>& c, int b, int chl, int chr, const cx<Tc>* x, cx<Tc>* y) {
   const int D = c.P->Dbond[b];
-  blk_gemm<Tc>(chl * D, chr, chl, matA(c.Lenv(b), chl, 1), matB(x, chr, 1), c.t1, chr, 1, c.gsm);
-  blk_gemm<Tc>(chl, chr, D * chr, matA(c.t1, (long long)D * chr, 1), matB(c.Renv(b), chr, 1), y, chr, 1, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * D, chr, chl, matA(c.Lenv(b), chl, 1), matB(x, chr, 1), c.t1, chr, 1, c.gsm));
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl, chr, D * chr, matA(c.t1, (long long)D * chr, 1), matB(c.Renv(b), chr, 1), y, chr, 1, c.gsm));
   count_contract(c, (double)chl * D * chr * chl + (double)chl * chr * D * chr);
 }
 
@@ -123,11 +143,11 @@ __device__ __noinline__ void env_left(const Ctx<Tc, Td>& c, int l) {
   const int chl = c.mps.chi[l], chr = c.mps.chi[l + 1];
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 1];
   const cx<Tc>* A = c.mps.site(l);
-  blk_gemm<Tc>(chl * Dl, kD * chr, chl, matA(c.Lenv(l), chl, 1), matB(A, kD * chr, 1), c.t1, kD * chr, 1, c.gsm);
-  blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
-                 (long long)kD * Dr * chr, chr, c.gsm);
-  blk_gemm<Tc>(chr, Dr * chr, chl * kD, matA(A, 1, chr, 1), matB(c.t2, (long long)Dr * chr, 1), c.Lenv(l + 1),
-               (long long)Dr * chr, 1, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, kD * chr, chl, matA(c.Lenv(l), chl, 1), matB(A, kD * chr, 1), c.t1, kD * chr, 1, c.gsm));
+  TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
+                 (long long)kD * Dr * chr, chr, c.gsm, site_shift(c), kD, Dr - 1, Dr, 0, 1));
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chr, Dr * chr, chl * kD, matA(A, 1, chr, 1), matB(c.t2, (long long)Dr * chr, 1), c.Lenv(l + 1),
+               (long long)Dr * chr, 1, c.gsm));
   count_contract(c, (double)chl * Dl * kD * chr * chl + (double)chl * chr * kD * Dr * Dl * kD +
                         (double)chr * Dr * chr * chl * kD);
 }
@@ -139,15 +159,15 @@ __device__ __noinline__ void env_right(const Ctx<Tc, Td>& c, int l) {
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 1];
   const cx<Tc>* B = c.mps.site(l);
   // S1[(a s)][v][y] = B[(a s), b] R_v[b, y]
-  blk_gemm_batched<Tc>(Dr, chl * kD, chr, chr, mk((Tc)1, (Tc)0), matA(B, chr, 1), 0,
+  TJM_TIMED(c, PH_GEMM, blk_gemm_batched<Tc>(Dr, chl * kD, chr, chr, mk((Tc)1, (Tc)0), matA(B, chr, 1), 0,
                        matB(c.Renv(l + 1), chr, 1), (long long)chr * chr, c.t1, (long long)Dr * chr, 1, chr, false,
-                       c.gsm);
+                       c.gsm));
   // S2[a][(w t)][y] = sum_(s v) WmR[(w t)][(s v)] S1[a][(s v)][y]
-  blk_wapply<Tc>(chl, Dl * kD, kD * Dr, chr, c.P->WmR + c.P->WmR_off[l], c.t1, (long long)kD * Dr * chr, chr, c.t2,
-                 (long long)Dl * kD * chr, chr, c.gsm);
+  TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, Dl * kD, kD * Dr, chr, c.P->WmR + c.P->WmR_off[l], c.t1, (long long)kD * Dr * chr, chr, c.t2,
+                 (long long)Dl * kD * chr, chr, c.gsm, site_shift(c), kD, 0, 1, Dr - 1, Dr));
   // Rnew[w][a][x] = S2[a][w][(t y)] conj(B[x][(t y)])
-  blk_gemm_batched<Tc>(Dl, chl, chl, kD * chr, mk((Tc)1, (Tc)0), matA(c.t2, (long long)Dl * kD * chr, 1), kD * chr,
-                       matB(B, 1, kD * chr, 1), 0, c.Renv(l), chl, 1, (long long)chl * chl, false, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm_batched<Tc>(Dl, chl, chl, kD * chr, mk((Tc)1, (Tc)0), matA(c.t2, (long long)Dl * kD * chr, 1), kD * chr,
+                       matB(B, 1, kD * chr, 1), 0, c.Renv(l), chl, 1, (long long)chl * chl, false, c.gsm));
   count_contract(c, (double)Dr * chl * kD * chr * chr + (double)chl * chr * Dl * kD * kD * Dr +
                         (double)Dl * chl * chl * kD * chr);
 }
@@ -159,6 +179,21 @@ __device__ void build_right_envs(const Ctx<Tc, Td>& c) {
   __syncthreads();
   for (int l = L - 1; l >= 1; --l) env_right(c, l);
   if (threadIdx.x == 0) atomicAdd(&c.S->stats.env_updates, (unsigned long long)(L - 1));
+  if (!c.P->shift_ok) return;
+  // <H - shift> of the right-canonical state from site 0 and its environment;
+  // the energy per site becomes the shift of the next environments
+  const int n0 = c.mps.chi[0] * kD * c.mps.chi[1];
+  heff1(c, 0, c.mps.site(0), c.w);
+  double e = 0.0, nn = 0.0;
+  for (int i = threadIdx.x; i < n0; i += TJM_THREADS) {
+    const cx<Tc> a = c.mps.site(0)[i], b = c.w[i];
+    e += (double)a.x * b.x + (double)a.y * b.y;
+    nn += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  e = blk_sum(e, c.red);
+  nn = blk_sum(nn, c.red + 16);
+  if (threadIdx.x == 0 && nn > 0.0 && e == e) c.S->eshift += e / nn / L;
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------ Lanczos exponential
@@ -184,58 +219,64 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
   int k = 0;
   for (;; ++k) {
     const cx<Tc>* vk = c.krylov + (long long)k * n;
-    if (kind == 1) heff1(c, l, vk, c.w);
-    else if (kind == 2) heff2(c, l, chl, chr, vk, c.w);
-    else heff0(c, l, chl, chr, vk, c.w);
-    // alpha_k = Re <v_k, w>
-    {
-      Tc acc = 0;
-      for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-        const cx<Tc> a = vk[i], b = c.w[i];
-        acc = fma(a.x, b.x, acc); acc = fma(a.y, b.y, acc);
-      }
-      const double al = blk_sum((double)acc, c.red);
-      if (threadIdx.x == 0) alpha[k] = al;
-    }
-    __syncthreads();
-    {
-      const Tc al = (Tc)alpha[k], bm = k > 0 ? (Tc)beta[k - 1] : (Tc)0;
-      const cx<Tc>* vm = k > 0 ? vk - n : vk;
-      for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-        cx<Tc> t = c.w[i];
-        t = t - al * vk[i];
-        if (k > 0) t = t - bm * vm[i];
-        c.w[i] = t;
-      }
-    }
-    __syncthreads();
+    TJM_TIMED(c, PH_MATVEC, {
+      if (kind == 1) heff1(c, l, vk, c.w);
+      else if (kind == 2) heff2(c, l, chl, chr, vk, c.w);
+      else heff0(c, l, chl, chr, vk, c.w);
+    });
+    // Orthogonalise w = H v_k against v_0..v_k by classical Gram-Schmidt,
+    // twice (the three-term recurrence is part of the projection; h_k = alpha_k).
+    // Each projection reads w once per chunk of 8 basis vectors to form all
+    // coefficients, then once more to subtract them while accumulating the new
+    // ||w||^2.  Coefficients are reduced in FP64.
+    const int nb = k + 1;
+    double wn2 = 0.0, al_k = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      const int nb = k + 1;
-      // h_j = <v_j, w>, j <= k  (per-thread partials, then FP64 block sums)
-      for (int j = 0; j < nb; ++j) {
-        const cx<Tc>* vj = c.krylov + (long long)j * n;
-        cx<Tc> acc = czero<Tc>();
-        for (int i = threadIdx.x; i < n; i += TJM_THREADS) cfma_cj(acc, vj[i], c.w[i]);
-        const double ax = warp_sum((double)acc.x), ay = warp_sum((double)acc.y);
-        if ((threadIdx.x & 31) == 0) {
-          c.red[(2 * j) * TJM_WARPS + (threadIdx.x >> 5)] = ax;
-          c.red[(2 * j + 1) * TJM_WARPS + (threadIdx.x >> 5)] = ay;
+      for (int j0 = 0; j0 < nb; j0 += 8) {
+        const int jn = nb - j0 < 8 ? nb - j0 : 8;
+        cx<Tc> acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = czero<Tc>();
+        for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
+          const cx<Tc> wi = c.w[i];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < jn) cfma_cj(acc[q], c.krylov[(long long)(j0 + q) * n + i], wi);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q < jn) {
+            const double ax = warp_sum((double)acc[q].x), ay = warp_sum((double)acc[q].y);
+            if ((threadIdx.x & 31) == 0) {
+              c.red[(2 * (j0 + q)) * TJM_WARPS + (threadIdx.x >> 5)] = ax;
+              c.red[(2 * (j0 + q) + 1) * TJM_WARPS + (threadIdx.x >> 5)] = ay;
+            }
+          }
         }
       }
       blk_sums_finish(2 * nb, c.red, hh);
+      al_k += hh[2 * k];
+      // coefficients converted once (FP64 -> working precision), not per element
+      cx<Tc>* hw = reinterpret_cast<cx<Tc>*>(c.red);
+      for (int j = threadIdx.x; j < nb; j += TJM_THREADS) hw[j] = mk((Tc)hh[2 * j], (Tc)hh[2 * j + 1]);
+      __syncthreads();
+      Tc n2 = 0;
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
         cx<Tc> t = c.w[i];
-        for (int j = 0; j < nb; ++j) {
-          const cx<Tc> h = mk((Tc)hh[2 * j], (Tc)hh[2 * j + 1]);
-          t = t - h * c.krylov[(long long)j * n + i];
-        }
+        for (int j = 0; j < nb; ++j) t = t - hw[j] * c.krylov[(long long)j * n + i];
         c.w[i] = t;
+        n2 = fma(t.x, t.x, n2);
+        n2 = fma(t.y, t.y, n2);
       }
-      __syncthreads();
+      wn2 = blk_sum((double)n2, c.red + 64);
     }
-    const double bk = sqrt(blk_nrm2sq(c.w, n, c.red));
-    if (threadIdx.x < 32) warp_expm_tridiag(k + 1, alpha, beta, theta, cf);
+    if (threadIdx.x == 0) alpha[k] = al_k;
     __syncthreads();
+    const double bk = sqrt(wn2);
+    TJM_TIMED(c, PH_EXPM, {
+      if (threadIdx.x < 32) warp_expm_tridiag(k + 1, alpha, beta, theta, cf);
+      __syncthreads();
+    });
     const bool stop = !(bk * sqrt(norm2(cf[k])) >= tol) || (k == kmax - 1);
     if (stop) break;
     if (threadIdx.x == 0) beta[k] = bk;
@@ -247,12 +288,12 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
     __syncthreads();
   }
   const int nk = k + 1;
+  cx<Tc>* cw = reinterpret_cast<cx<Tc>*>(c.red);
+  for (int j = threadIdx.x; j < nk; j += TJM_THREADS) cw[j] = mk((Tc)(b0 * cf[j].x), (Tc)(b0 * cf[j].y));
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
     cx<Tc> acc = czero<Tc>();
-    for (int j = 0; j < nk; ++j) {
-      const cx<double> cj = cf[j];
-      cfma(acc, mk((Tc)(b0 * cj.x), (Tc)(b0 * cj.y)), c.krylov[(long long)j * n + i]);
-    }
+    for (int j = 0; j < nk; ++j) cfma(acc, cw[j], c.krylov[(long long)j * n + i]);
     v[i] = acc;
   }
   __syncthreads();
@@ -266,24 +307,32 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
 
 // ------------------------------------------------------------------ factorizations on site tensors
 // QR of the (rows x cols) matrix whose (i, j) element is src[i*si + j*sj]
-// (conjugated if cj).  Leaves Q (rows x k) in c.du and R (k x cols) in c.dv,
-// both column-major Td.  Returns k = min(rows, cols).
+// (conjugated if cj), in the factorization precision Td.  The thin Q (rows x k,
+// column-major) is formed in place in the workspace -- shared memory when the
+// matrix fits there, else the global buffer c.da -- and returned through *Q;
+// R (k x cols, column-major) is left in c.dv.  Returns k = min(rows, cols).
 template <class Tc, class Td>
-__device__ __noinline__ int qr_of(const Ctx<Tc, Td>& c, int rows, int cols, const cx<Tc>* src, long long si, long long sj, bool cj) {
+__device__ __noinline__ int qr_of(const Ctx<Tc, Td>& c, int rows, int cols, const cx<Tc>* src, long long si,
+                                  long long sj, bool cj, const cx<Td>** Q) {
+  const bool in_smem = (long long)c.fsm_bytes >= (long long)rows * cols * (long long)sizeof(cx<Td>);
+  cx<Td>* a = in_smem ? reinterpret_cast<cx<Td>*>(c.fsm) : c.da;
   for (long long e = threadIdx.x; e < (long long)rows * cols; e += TJM_THREADS) {
     const int i = (int)(e % rows), j = (int)(e / rows);
     cx<Tc> x = src[i * si + j * sj];
     if (cj) x.y = -x.y;
-    c.da[e] = cvt<Td>(x);
+    a[e] = cvt<Td>(x);
   }
   __syncthreads();
-  blk_qr<Td>(rows, cols, c.da, c.du, c.dv, c.drd, c.dtau, c.red);
-  __syncthreads();
+  TJM_TIMED(c, PH_QR, {
+    blk_qr<Td>(rows, cols, a, a, c.dv, c.drd, c.dtau, c.red);
+    __syncthreads();
+  });
   {
     const double k = rows < cols ? rows : cols;
     // Householder factorization and explicit thin Q: 2 (m n^2 - n^3/3) complex multiply-adds each way
     count_decomp(c, 4.0 * ((double)rows * cols * k - k * k * k / 3.0));
   }
+  *Q = a;
   return rows < cols ? rows : cols;
 }
 
@@ -294,10 +343,11 @@ __device__ int qr_right(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int l) {
   const int chl = m.chi[l], chr = m.chi[l + 1];
   const int rows = chl * kD;
   cx<Tc>* M = m.site(l);
-  const int k = qr_of(c, rows, chr, M, chr, 1, false);
+  const cx<Td>* Q;
+  const int k = qr_of(c, rows, chr, M, chr, 1, false, &Q);
   for (long long e = threadIdx.x; e < (long long)rows * k; e += TJM_THREADS) {
     const int i = (int)(e / k), j = (int)(e % k);
-    M[e] = cvt<Tc>(c.du[(long long)j * rows + i]);
+    M[e] = cvt<Tc>(Q[(long long)j * rows + i]);
   }
   for (long long e = threadIdx.x; e < (long long)k * chr; e += TJM_THREADS) {
     const int i = (int)(e / chr), j = (int)(e % chr);
@@ -317,11 +367,12 @@ __device__ int rq_left(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int l) {
   const int cols = kD * chr;
   cx<Tc>* M = m.site(l);
   // A = M^H : (cols x chl), A(i, j) = conj(M[j][i])
-  const int k = qr_of(c, cols, chl, M, 1, cols, true);
+  const cx<Td>* Q;
+  const int k = qr_of(c, cols, chl, M, 1, cols, true, &Q);
   // new M = Q^H : (k x cols)
   for (long long e = threadIdx.x; e < (long long)k * cols; e += TJM_THREADS) {
     const int i = (int)(e / cols), j = (int)(e % cols);
-    M[e] = cvt<Tc>(conj(c.du[(long long)i * cols + j]));
+    M[e] = cvt<Tc>(conj(Q[(long long)i * cols + j]));
   }
   // C = R^H : (chl x k), R is (k x chl) column-major in dv
   for (long long e = threadIdx.x; e < (long long)chl * k; e += TJM_THREADS) {
@@ -339,7 +390,7 @@ template <class Tc, class Td>
 __device__ void absorb_right(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int l, int chi_old) {
   const int k = m.chi[l + 1], chn = m.chi[l + 2];
   cx<Tc>* M = m.site(l + 1);
-  blk_gemm<Tc>(k, kD * chn, chi_old, matA(c.bond, chi_old, 1), matB(M, kD * chn, 1), c.tmp, kD * chn, 1, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(k, kD * chn, chi_old, matA(c.bond, chi_old, 1), matB(M, kD * chn, 1), c.tmp, kD * chn, 1, c.gsm));
   blk_copy(M, c.tmp, k * kD * chn);
   __syncthreads();
 }
@@ -349,7 +400,7 @@ template <class Tc, class Td>
 __device__ void absorb_left(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int l, int chi_old) {
   const int k = m.chi[l], chp = m.chi[l - 1];
   cx<Tc>* M = m.site(l - 1);
-  blk_gemm<Tc>(chp * kD, k, chi_old, matA(M, chi_old, 1), matB(c.bond, k, 1), c.tmp, k, 1, c.gsm);
+  TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chp * kD, k, chi_old, matA(M, chi_old, 1), matB(c.bond, k, 1), c.tmp, k, 1, c.gsm));
   blk_copy(M, c.tmp, chp * kD * k);
   __syncthreads();
 }
@@ -388,15 +439,22 @@ template <class Tc, class Td>
 __device__ __noinline__ int svd_of(const Ctx<Tc, Td>& c, int m, int n, const cx<Tc>* src, long long si, long long sj) {
   const bool tr = m < n;
   const int mm = tr ? n : m, nn = tr ? m : n;
-  // work matrix (mm x nn): A or A^H
+  // work matrix (mm x nn): A or A^H, in shared memory when it fits (the GEMM
+  // staging area then holds the rotation accumulator)
+  const bool in_smem = (long long)c.fsm_bytes >= (long long)mm * nn * (long long)sizeof(cx<Td>) &&
+                       (long long)nn * nn * (long long)sizeof(cx<Td>) <= kSmemGemm;
+  cx<Td>* a = in_smem ? reinterpret_cast<cx<Td>*>(c.fsm) : c.da;
+  cx<Td>* vw = in_smem ? reinterpret_cast<cx<Td>*>(c.gsm) : c.dvw;
+  Td* sv = in_smem ? reinterpret_cast<Td*>(c.fsv) : reinterpret_cast<Td*>(c.dvw + (long long)nn * nn);
   for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) {
     const int i = (int)(e % mm), j = (int)(e / mm);
     cx<Tc> x = tr ? conj(src[j * si + i * sj]) : src[i * si + j * sj];
-    c.da[e] = cvt<Td>(x);
+    a[e] = cvt<Td>(x);
   }
   __syncthreads();
   // on the work matrix: Wk = Uw diag(s) Vw^H; Uw -> du (mm x nn), Vw -> dv (nn x nn)
-  const int sweeps = blk_svd_jacobi<Td>(mm, nn, c.da, c.du, c.ds, c.dv, c.dvw, c.iw, c.red, c.P->exact != 0);
+  int sweeps = 0;
+  TJM_TIMED(c, PH_SVD, sweeps = blk_svd_jacobi<Td>(mm, nn, a, c.du, c.ds, c.dv, vw, sv, c.iw, c.red, c.P->exact != 0));
   // per sweep and pair: three column dot products and two column rotations (A and V)
   count_decomp(c, (double)(sweeps + 1) * 0.5 * nn * (nn - 1) * (3.0 * mm + 2.0 * (mm + nn)));
   if (tr) {
@@ -428,7 +486,7 @@ __device__ __noinline__ void tdvp_sweep(const Ctx<Tc, Td>& c, double tau) {
       blk_gemm<Tc>(chl * kD, kD * chr, chb, matA(m.site(l), chb, 1), matB(m.site(l + 1), kD * chr, 1), c.theta,
                    kD * chr, 1, c.gsm);
       const int n = chl * kD * kD * chr;
-      lanczos(c, 2, l, chl, chr, c.theta, n, -tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 2, l, chl, chr, c.theta, n, -tau));
       const int nn = svd_of(c, chl * kD, kD * chr, c.theta, kD * chr, 1);
       const int r = trunc_rank(c, nn);
       cx<Tc>* A = m.site(l);
@@ -446,18 +504,18 @@ __device__ __noinline__ void tdvp_sweep(const Ctx<Tc, Td>& c, double tau) {
       if (threadIdx.x == 0) m.chi[l + 1] = r;
       __syncthreads();
       env_left(c, l);
-      if (l + 1 < L - 1) lanczos(c, 1, l + 1, 0, 0, m.site(l + 1), r * kD * chr, +tau);
+      if (l + 1 < L - 1) TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, l + 1, 0, 0, m.site(l + 1), r * kD * chr, +tau));
       last_two = true;
     } else {
-      lanczos(c, 1, l, 0, 0, m.site(l), chl * kD * chb, -tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, l, 0, 0, m.site(l), chl * kD * chb, -tau));
       const int k = qr_right(c, m, l);
       env_left(c, l);
-      lanczos(c, 0, l + 1, k, chb, c.bond, k * chb, +tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 0, l + 1, k, chb, c.bond, k * chb, +tau));
       absorb_right(c, m, l, chb);
       last_two = false;
     }
   }
-  if (!last_two) lanczos(c, 1, L - 1, 0, 0, m.site(L - 1), m.chi[L - 1] * kD * m.chi[L], -tau);
+  if (!last_two) TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, L - 1, 0, 0, m.site(L - 1), m.chi[L - 1] * kD * m.chi[L], -tau));
   last_two = false;
   for (int l = L - 1; l >= 1; --l) {
     const int chl = m.chi[l - 1], chb = m.chi[l], chr = m.chi[l + 1];
@@ -465,7 +523,7 @@ __device__ __noinline__ void tdvp_sweep(const Ctx<Tc, Td>& c, double tau) {
       blk_gemm<Tc>(chl * kD, kD * chr, chb, matA(m.site(l - 1), chb, 1), matB(m.site(l), kD * chr, 1), c.theta,
                    kD * chr, 1, c.gsm);
       const int n = chl * kD * kD * chr;
-      lanczos(c, 2, l - 1, chl, chr, c.theta, n, -tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 2, l - 1, chl, chr, c.theta, n, -tau));
       const int nn = svd_of(c, chl * kD, kD * chr, c.theta, kD * chr, 1);
       const int r = trunc_rank(c, nn);
       cx<Tc>* A = m.site(l - 1);
@@ -483,18 +541,18 @@ __device__ __noinline__ void tdvp_sweep(const Ctx<Tc, Td>& c, double tau) {
       if (threadIdx.x == 0) m.chi[l] = r;
       __syncthreads();
       env_right(c, l);
-      if (l - 1 > 0) lanczos(c, 1, l - 1, 0, 0, m.site(l - 1), chl * kD * r, +tau);
+      if (l - 1 > 0) TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, l - 1, 0, 0, m.site(l - 1), chl * kD * r, +tau));
       last_two = true;
     } else {
-      lanczos(c, 1, l, 0, 0, m.site(l), chb * kD * chr, -tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, l, 0, 0, m.site(l), chb * kD * chr, -tau));
       const int k = rq_left(c, m, l);
       env_right(c, l);
-      lanczos(c, 0, l, chb, k, c.bond, chb * k, +tau);
+      TJM_TIMED(c, PH_LANCZOS, lanczos(c, 0, l, chb, k, c.bond, chb * k, +tau));
       absorb_left(c, m, l, chb);
       last_two = false;
     }
   }
-  if (!last_two) lanczos(c, 1, 0, 0, 0, m.site(0), m.chi[0] * kD * m.chi[1], -tau);
+  if (!last_two) TJM_TIMED(c, PH_LANCZOS, lanczos(c, 1, 0, 0, 0, m.site(0), m.chi[0] * kD * m.chi[1], -tau));
   if (threadIdx.x == 0) atomicAdd(&c.S->stats.env_updates, (unsigned long long)(2 * (L - 1)));
 }
 
@@ -512,7 +570,7 @@ __device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m
     const int chl = m.chi[l], chr = m.chi[l + 1];
     const cx<Tc>* M = m.site(l);
     // F[a'][(s b)] = E[a'][a] M[a][(s b)]
-    blk_gemm<Tc>(chl, kD * chr, chl, matA(c.E, chl, 1), matB(M, kD * chr, 1), c.F, kD * chr, 1, c.gsm);
+    TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl, kD * chr, chl, matA(c.E, chl, 1), matB(M, kD * chr, 1), c.F, kD * chr, 1, c.gsm));
     // G[t][s] = sum_(a' b) conj(M[a'][t][b]) F[a'][s][b]
     cx<Tc> g[4] = {czero<Tc>(), czero<Tc>(), czero<Tc>(), czero<Tc>()};
     for (int e = threadIdx.x; e < chl * chr; e += TJM_THREADS) {
@@ -533,7 +591,7 @@ __device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m
       for (int q = 0; q < 4; ++q) c.G[(long long)l * 4 + q] = mk(c.sc[448 + 2 * q], c.sc[448 + 2 * q + 1]);
     // E'[b'][b] = sum_(a' s) conj(M[a'][s][b']) F[a'][s][b]
     if (l + 1 < L)
-      blk_gemm<Tc>(chr, chr, chl * kD, matA(M, 1, chr, 1), matB(c.F, chr, 1), c.E, chr, 1, c.gsm);
+      TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chr, chr, chl * kD, matA(M, 1, chr, 1), matB(c.F, chr, 1), c.E, chr, 1, c.gsm));
     __syncthreads();
   }
 }

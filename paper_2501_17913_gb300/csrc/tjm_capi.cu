@@ -75,7 +75,7 @@ struct tjm_ctx {
   std::string err;
   int64_t launches = 0;
   // problem
-  int L = 0, chi_max = 0, n_jumps = 0, Dmax = 1;
+  int L = 0, chi_max = 0, n_jumps = 0, Dmax = 1, shift_ok = 0;
   double dt = 0, trunc_eps = 0;
   std::vector<int> Dbond;
   std::vector<zc> Wm1, WmR, W12, Dhalf, Dfull, jop, jLdL;
@@ -260,6 +260,7 @@ void tjm_default_options(tjm_options* o) {
   o->exact_full_bond = 0;
   o->device = 0;
   o->max_ctas = 0;
+  o->energy_shift = 1;
 }
 
 const char* tjm_last_error(const tjm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -315,6 +316,29 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
     const int Dr = ctx->Dbond[l + 1];
     return ctx->Wsite[l][(((size_t)w * Dr + v) * d + t) * d + s];
   };
+  // Finite-state form: channel 0 carries the identity string from the left
+  // (column 0 is I in row 0 and zero below it) and the last channel carries it
+  // to the right (the last row is I in the last column and zero before it).
+  // Then adding -s*I to each site's entry (0, last) adds -s*L*I to H.
+  ctx->shift_ok = 1;
+  for (int b = 1; b < L; ++b)
+    if (ctx->Dbond[b] < 2) ctx->shift_ok = 0;
+  auto is_id = [&](int l, int w, int v, double scale) {
+    for (int t = 0; t < d; ++t)
+      for (int s = 0; s < d; ++s)
+        if (Wel(l, w, v, t, s) != zc(t == s ? scale : 0.0)) return false;
+    return true;
+  };
+  for (int l = 0; l < L && ctx->shift_ok; ++l) {
+    const int Dl = ctx->Dbond[l], Dr = ctx->Dbond[l + 1];
+    if (l + 1 < L)
+      for (int w = 0; w < Dl; ++w)
+        if (!is_id(l, w, 0, w == 0 ? 1.0 : 0.0)) ctx->shift_ok = 0;
+    if (l > 0)
+      for (int v = 0; v < Dr; ++v)
+        if (!is_id(l, Dl - 1, v, v == Dr - 1 ? 1.0 : 0.0)) ctx->shift_ok = 0;
+  }
+  if (!ctx->opt.energy_shift) ctx->shift_ok = 0;
   // kernel layouts of the MPO
   for (int l = 0; l < L; ++l) {
     const int Dl = ctx->Dbond[l], Dr = ctx->Dbond[l + 1];
@@ -526,7 +550,7 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   // problem descriptor of this run
   tjm::ProbDev P;
   std::memset(&P, 0, sizeof P);
-  P.L = L; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
+  P.L = L; P.shift_ok = ctx->shift_ok; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
   P.n_jumps = ctx->n_jumps; P.n_obs = n_obs; P.n_steps = R.n_steps; P.n_samples = n_times;
   P.dt = dt; P.trunc_eps = ctx->trunc_eps; P.krylov_tol = ctx->opt.krylov_tol;
   P.Dbond = ctx->d_Dbond;
@@ -783,6 +807,7 @@ tjm_status tjm_run_stats(tjm_ctx* ctx, int64_t run_id, tjm_stats* out) {
     out->min_margin_pick = std::min(out->min_margin_pick, S.stats.min_margin2);
     out->flops_contract += S.stats.flops_contract;
     out->flops_decomp += S.stats.flops_decomp;
+    for (int q = 0; q < 12; ++q) out->cycles[q] += S.stats.cyc[q];
   }
   std::vector<int> chi((size_t)R->n_traj * (R->L + 1));
   TJM_CU(cudaMemcpy(chi.data(), R->chi, chi.size() * sizeof(int), cudaMemcpyDeviceToHost));

@@ -49,6 +49,50 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Compensated warp sum of FP32 values: each lane carries (hi, lo) with
+// hi + lo exact; partner pairs are added with Knuth's TwoSum (the rounding
+// error of hi1 + hi2 recovered exactly) and the low parts summed on top
+// (Dekker's double-length addition).  The result is the sum correctly rounded
+// up to a few units of 2^-48 -- the accuracy of an FP64 reduction at the cost
+// of FP32 instructions, which GB300 issues 64x faster than FP64.
+struct f2s { float hi, lo; };
+__device__ __forceinline__ f2s df_add(f2s a, f2s b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ void warp_sum_df4(float& v0, float& v1, float& v2, float& v3) {
+  f2s a = {v0, 0.f}, b = {v1, 0.f}, c = {v2, 0.f}, d = {v3, 0.f};
+  for (int o = 16; o > 0; o >>= 1) {
+    a = df_add(a, {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+    b = df_add(b, {__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o)});
+    c = df_add(c, {__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o)});
+    d = df_add(d, {__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)});
+  }
+  v0 = a.hi + a.lo; v1 = b.hi + b.lo; v2 = c.hi + c.lo; v3 = d.hi + d.lo;
+}
+__device__ __forceinline__ void warp_sum_df2(float& v0, float& v1) {
+  f2s a = {v0, 0.f}, b = {v1, 0.f};
+  for (int o = 16; o > 0; o >>= 1) {
+    a = df_add(a, {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+    b = df_add(b, {__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o)});
+  }
+  v0 = a.hi + a.lo; v1 = b.hi + b.lo;
+}
+// Accurate warp sums in the factorization precision: FP64 shuffles for
+// double, compensated FP32 for float.
+__device__ __forceinline__ void warp_sum_acc4(double& v0, double& v1, double& v2, double& v3) {
+  v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2); v3 = warp_sum(v3);
+}
+__device__ __forceinline__ void warp_sum_acc4(float& v0, float& v1, float& v2, float& v3) {
+  warp_sum_df4(v0, v1, v2, v3);
+}
+__device__ __forceinline__ void warp_sum_acc2(double& v0, double& v1) { v0 = warp_sum(v0); v1 = warp_sum(v1); }
+__device__ __forceinline__ void warp_sum_acc2(float& v0, float& v1) { warp_sum_df2(v0, v1); }
+
 __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;

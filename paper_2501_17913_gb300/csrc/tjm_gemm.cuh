@@ -23,27 +23,35 @@ template <class T> __host__ __device__ inline MatB<T> matB(const cx<T>* p, long 
 }
 
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+// bytes of shared memory reserved for GEMM staging (two 16-deep tiles of 64 complex doubles)
+constexpr int kSmemGemm = 32768;
 template <class T> constexpr int gemm_smem_bytes() { return 2 * GB_K * GB_M * (int)sizeof(cx<T>); }
 
-// Batched: for b < batch, operands offset by (sa, sb, sc) elements.
-template <class T>
-__device__ __noinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx<T> alpha, MatA<T> A, long long sa, MatB<T> B,
-                                 long long sb, cx<T>* C, long long sci, long long scj, long long sc, bool accumulate,
-                                 char* smem) {
+// One layout variant: AK = A's k index is contiguous (else its i index),
+// BJ = B's j index is contiguous (else its k index).  Each thread loads 4
+// elements of A and 4 of B per 16-deep slice; their tile coordinates are fixed
+// per thread, so the loads need no per-element index arithmetic.
+template <class T, bool AK, bool BJ>
+__device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* __restrict__ A,
+                                       int sai, int sak, int ca, long long sa, const cx<T>* __restrict__ B, int sbk,
+                                       int sbj, int cb, long long sb, cx<T>* C, int sci, int scj, long long sc,
+                                       bool accumulate, char* smem) {
   cx<T>* As = reinterpret_cast<cx<T>*>(smem);          // [GB_K][GB_M]
   cx<T>* Bs = As + GB_K * GB_M;                          // [GB_K][GB_N]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int a_i = AK ? (tid >> 4) : (tid & 63);          // + 16 q   (AK)
+  const int a_k = AK ? (tid & 15) : (tid >> 6);          // + 4 q    (!AK)
+  const int b_j = BJ ? (tid & 63) : (tid >> 4);          // + 16 q   (!BJ)
+  const int b_k = BJ ? (tid >> 6) : (tid & 15);          // + 4 q    (BJ)
   const int tm = (M + GB_M - 1) / GB_M, tn = (N + GB_N - 1) / GB_N;
   const int ntile = batch * tm * tn;
   const int nk = (K + GB_K - 1) / GB_K;
-  const bool a_kfast = (A.sk == 1);
-  const bool b_jfast = (B.sj == 1) || (B.sk != 1);
-  if (M <= 0 || N <= 0) return;
+  const T sga = ca ? (T)-1 : (T)1, sgb = cb ? (T)-1 : (T)1;
   for (int t = 0; t < ntile; ++t) {
-    const int b = t / (tm * tn), r0 = t % (tm * tn);
+    const int bt = t / (tm * tn), r0 = t % (tm * tn);
     const int i0 = (r0 / tn) * GB_M, j0 = (r0 % tn) * GB_N;
-    const cx<T>* Ap = A.p + b * sa;
-    const cx<T>* Bp = B.p + b * sb;
+    const cx<T>* Ap = A + bt * sa;
+    const cx<T>* Bp = B + bt * sb;
     cx<T> acc[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -53,37 +61,26 @@ __device__ __noinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx
     auto load = [&](int k0) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int e = tid + TJM_THREADS * q;
-        int ii, kk;
-        if (a_kfast) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
-        const int i = i0 + ii, k = k0 + kk;
+        const int i = i0 + a_i + (AK ? 16 * q : 0), k = k0 + a_k + (AK ? 0 : 4 * q);
         cx<T> v = czero<T>();
-        if (i < M && k < K) { v = Ap[i * A.si + k * A.sk]; if (A.conj) v.y = -v.y; }
+        if (i < M && k < K) v = Ap[i * sai + k * sak];
+        v.y *= sga;
         ra[q] = v;
-        int jj, kb;
-        if (b_jfast) { jj = e & 63; kb = e >> 6; } else { kb = e & 15; jj = e >> 4; }
-        const int j = j0 + jj, kq = k0 + kb;
+        const int j = j0 + b_j + (BJ ? 0 : 16 * q), kb = k0 + b_k + (BJ ? 4 * q : 0);
         cx<T> u = czero<T>();
-        if (j < N && kq < K) { u = Bp[kq * B.sk + j * B.sj]; if (B.conj) u.y = -u.y; }
+        if (j < N && kb < K) u = Bp[kb * sbk + j * sbj];
+        u.y *= sgb;
         rb[q] = u;
-      }
-    };
-    auto store = [&]() {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = tid + TJM_THREADS * q;
-        int ii, kk;
-        if (a_kfast) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
-        As[kk * GB_M + ii] = ra[q];
-        int jj, kb;
-        if (b_jfast) { jj = e & 63; kb = e >> 6; } else { kb = e & 15; jj = e >> 4; }
-        Bs[kb * GB_N + jj] = rb[q];
       }
     };
     load(0);
     for (int ks = 0; ks < nk; ++ks) {
       __syncthreads();
-      store();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        As[(a_k + (AK ? 0 : 4 * q)) * GB_M + a_i + (AK ? 16 * q : 0)] = ra[q];
+        Bs[(b_k + (BJ ? 4 * q : 0)) * GB_N + b_j + (BJ ? 0 : 16 * q)] = rb[q];
+      }
       __syncthreads();
       if (ks + 1 < nk) load((ks + 1) * GB_K);
 #pragma unroll 4
@@ -99,7 +96,7 @@ __device__ __noinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx
           for (int c = 0; c < 4; ++c) cfma(acc[r][c], a[r], bb[c]);
       }
     }
-    cx<T>* Cp = C + b * sc;
+    cx<T>* Cp = C + bt * sc;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int i = i0 + ty + 16 * r;
@@ -118,6 +115,28 @@ __device__ __noinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx
   __syncthreads();
 }
 
+// Batched: for b < batch, operands offset by (sa, sb, sc) elements.
+template <class T>
+__device__ __forceinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx<T> alpha, MatA<T> A,
+                                                 long long sa, MatB<T> B, long long sb, cx<T>* C, long long sci,
+                                                 long long scj, long long sc, bool accumulate, char* smem) {
+  if (M <= 0 || N <= 0) return;
+  const bool ak = A.sk == 1;
+  const bool bj = (B.sj == 1) || (B.sk != 1);
+  if (ak && bj)
+    gemm_core<T, true, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
+                             B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else if (ak)
+    gemm_core<T, true, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
+                              B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else if (bj)
+    gemm_core<T, false, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
+                              B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else
+    gemm_core<T, false, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
+                               (int)B.sj, B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+}
+
 template <class T>
 __device__ __forceinline__ void blk_gemm(int M, int N, int K, MatA<T> A, MatB<T> B, cx<T>* C, long long sci,
                                          long long scj, char* smem, cx<T> alpha = mk((T)1, (T)0),
@@ -127,14 +146,51 @@ __device__ __forceinline__ void blk_gemm(int M, int N, int K, MatA<T> A, MatB<T>
 
 // out[p][o][q] = sum_i Wm[o][i] in[p][i][q] -- the small MPO contraction
 // between the two big GEMMs of an effective-Hamiltonian application.
-// Wm (O x I, complex double, row-major) is staged in shared memory in the
-// working precision; zero entries of the MPO are skipped.
+// Wm (O x I <= 32 x 32, complex double, row-major) is compressed by warp 0
+// into a row-sparse list in shared memory (the MPO is mostly zeros), then
+// every thread handles (p, q) pairs reading only the inputs that matter.
+//
+// A scalar `shift` can be added on nsh diagonal entries (o, i) =
+// (so0 + t * so_step, si0 + t * si_step), t < nsh: this is how a constant
+// times the identity rides on an MPO's on-site channel.
 template <class T>
-__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* in, long long sip,
-                           long long sii, cx<T>* out, long long sop, long long soo, char* smem) {
-  cx<T>* Ws = reinterpret_cast<cx<T>*>(smem);
+__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* in,
+                                        long long sip, long long sii, cx<T>* out, long long sop, long long soo,
+                                        char* smem, double shift = 0.0, int nsh = 0, int so0 = 0, int so_step = 1,
+                                        int si0 = 0, int si_step = 1) {
+  cx<T>* val = reinterpret_cast<cx<T>*>(smem);                      // [O * I]
+  int* col = reinterpret_cast<int*>(val + O * I);                    // [O * I]
+  int* rp = col + O * I;                                             // [O + 1]
   __syncthreads();
-  for (int e = threadIdx.x; e < O * I; e += TJM_THREADS) Ws[e] = cvt<T>(Wm[e]);
+  if (threadIdx.x < 32) {
+    const int o = threadIdx.x;
+    int ish = -1;                       // column of this row's shift entry, if any
+    if (shift != 0.0 && o >= so0 && (o - so0) % so_step == 0 && (o - so0) / so_step < nsh)
+      ish = si0 + ((o - so0) / so_step) * si_step;
+    int cnt = 0;
+    if (o < O)
+      for (int i = 0; i < I; ++i) {
+        cx<double> w = Wm[o * I + i];
+        if (i == ish) w.x += shift;
+        cnt += (w.x != 0.0 || w.y != 0.0);
+      }
+    int incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (o >= d) incl += v;
+    }
+    const int start = incl - cnt;
+    if (o < O) {
+      rp[o] = start;
+      if (o == O - 1) rp[O] = incl;
+      int pos = start;
+      for (int i = 0; i < I; ++i) {
+        cx<double> w = Wm[o * I + i];
+        if (i == ish) w.x += shift;
+        if (w.x != 0.0 || w.y != 0.0) { val[pos] = cvt<T>(w); col[pos] = i; ++pos; }
+      }
+    }
+  }
   __syncthreads();
   const long long tot = (long long)P * Q;
   for (long long e = threadIdx.x; e < tot; e += TJM_THREADS) {
@@ -143,11 +199,8 @@ __device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<dou
     cx<T>* dst = out + p * sop + q;
     for (int o = 0; o < O; ++o) {
       cx<T> acc = czero<T>();
-      const cx<T>* wr = Ws + o * I;
-      for (int i = 0; i < I; ++i) {
-        const cx<T> w = wr[i];
-        if (w.x != (T)0 || w.y != (T)0) cfma(acc, w, src[i * sii]);
-      }
+      const int e1 = rp[o + 1];
+      for (int z = rp[o]; z < e1; ++z) cfma(acc, val[z], src[col[z] * sii]);
       dst[o * soo] = acc;
     }
   }

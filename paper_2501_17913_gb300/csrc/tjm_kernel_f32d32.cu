@@ -8,16 +8,16 @@ namespace tjm {
 cudaError_t launch_f32d32(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
                       char* scratch, long long stride, ScratchDims dims) {
   auto kern = advance_kernel<float, float>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float>());
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, kSmemBytes, s>>>(order, n, next, max_steps, scratch, stride, dims);
+  kern<<<ctas, TJM_THREADS, smem_bytes<float>(), s>>>(order, n, next, max_steps, scratch, stride, dims);
   return cudaGetLastError();
 }
 
 int occupancy_f32d32() {
   int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, float>, TJM_THREADS, kSmemBytes);
+  cudaFuncSetAttribute(advance_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, float>, TJM_THREADS, smem_bytes<float>());
   return per_sm;
 }
 

@@ -7,6 +7,11 @@
 #pragma once
 #include "tjm_algo.cuh"
 
+// CTAs per SM the register allocation must allow (2: at most 128 registers per thread).
+#ifndef TJM_MIN_BLOCKS
+#define TJM_MIN_BLOCKS 2
+#endif
+
 namespace tjm {
 
 // Byte offsets of the per-CTA scratch; the same arithmetic runs on the host
@@ -49,8 +54,14 @@ __host__ __device__ inline ScratchMap scratch_map(const ScratchDims& d, int szc,
   return m;
 }
 
-constexpr int kSmemGemm = 32768;
-constexpr int kSmemBytes = kSmemGemm + 512 * 8 + 512 * 8;
+// Dynamic shared memory: GEMM staging, reductions, scalars, and -- for the
+// FP32 factorization precision -- a 64 KB workspace that holds the QR / SVD
+// matrix of a one-site update (up to 128 x 64 complex) plus its singular values.
+// FP64 factorizations keep their workspace in global memory and leave the
+// rest of the SM's L1 to cache it.
+constexpr int kSmemBase = kSmemGemm + 512 * 8 + 512 * 8;
+constexpr int kFsmBytes = 65536;
+template <class Td> constexpr int smem_bytes() { return sizeof(Td) == 4 ? kSmemBase + kFsmBytes + 1024 : kSmemBase; }
 
 template <class Tc, class Td>
 __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDims& dims, char* smem) {
@@ -88,6 +99,15 @@ __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDim
   c.gsm = smem;
   c.red = reinterpret_cast<double*>(smem + kSmemGemm);
   c.sc = c.red + 512;
+  if (sizeof(Td) == 4) {
+    c.fsm = smem + kSmemBase;
+    c.fsm_bytes = kFsmBytes;
+    c.fsv = smem + kSmemBase + kFsmBytes;
+  } else {
+    c.fsm = nullptr;
+    c.fsm_bytes = 0;
+    c.fsv = nullptr;
+  }
 }
 
 template <class Tc, class Td>
@@ -149,14 +169,14 @@ __device__ bool finish_step(const Ctx<Tc, Td>& c, int j, bool sample) {
     copy_mps(c, c.xmps, c.mps);
     double u1, u2;
     tjm_uniforms(S->seed, S->traj_id, (uint32_t)j, 1, &u1, &u2);
-    ok = dissipate_jump(c, c.xmps, P->Dhalf, u1, u2);
-    if (ok) measure(c, c.xmps, P->sample_row[j]);
+    TJM_TIMED(c, PH_DJ, ok = dissipate_jump(c, c.xmps, P->Dhalf, u1, u2));
+    if (ok) TJM_TIMED(c, PH_MEASURE, measure(c, c.xmps, P->sample_row[j]));
   }
   if (ok && j < P->n_steps) {
     double u1, u2;
     tjm_uniforms(S->seed, S->traj_id, (uint32_t)j, 0, &u1, &u2);
-    ok = dissipate_jump(c, c.mps, P->Dfull, u1, u2);
-    if (ok) build_right_envs(c);
+    TJM_TIMED(c, PH_DJ, ok = dissipate_jump(c, c.mps, P->Dfull, u1, u2));
+    if (ok) TJM_TIMED(c, PH_ENVBUILD, build_right_envs(c));
   }
   return ok;
 }
@@ -175,6 +195,7 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   int flags = S->flags;
   bool ok = true;
   if (step < 0) {
+    const long long t_init = clock64();
     ok = init_state(c);
     if (ok && P->sample_row[0] >= 0) measure(c, c.mps, P->sample_row[0]);
     if (ok && P->n_steps > 0) {
@@ -185,13 +206,14 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
     }
     step = 0;
     flags = 0;
+    if (threadIdx.x == 0) S->stats.cyc[PH_INIT] += (unsigned long long)(clock64() - t_init);
   } else if (flags & 1) {
     ok = canonicalise(c);
     if (ok) build_right_envs(c);
     flags &= ~1;
   }
   if (ok && max_steps == -1 && !(flags & 2) && step < P->n_steps) {
-    tdvp_sweep(c, 0.5 * P->dt);
+    TJM_TIMED(c, PH_TDVP, tdvp_sweep(c, 0.5 * P->dt));
     flags |= 2;
   } else if (ok && max_steps == -2 && (flags & 2)) {
     ok = finish_step(c, step + 1, false);
@@ -207,7 +229,7 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
     }
     while (ok && step < P->n_steps && done < max_steps) {
       const int j = step + 1;
-      tdvp_sweep(c, 0.5 * P->dt);
+      TJM_TIMED(c, PH_TDVP, tdvp_sweep(c, 0.5 * P->dt));
       ok = finish_step(c, j, true);
       step = j;
       ++done;
@@ -223,7 +245,7 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
 }
 
 template <class Tc, class Td>
-__global__ void __launch_bounds__(TJM_THREADS, 2)
+__global__ void __launch_bounds__(TJM_THREADS, TJM_MIN_BLOCKS)
 advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, char* scratch, long long stride,
                ScratchDims dims) {
   extern __shared__ __align__(16) char smem[];

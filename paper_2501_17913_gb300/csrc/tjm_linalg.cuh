@@ -20,7 +20,9 @@ template <> struct eps_of<double> { static constexpr double v = 2.22044604925031
 // ------------------------------------------------------------------ QR
 // a: m x n column-major (lda = m), factorised in place.  k = min(m, n).
 // On exit q (m x k, column-major) holds the thin Q, r (k x n, column-major,
-// ldr = k) holds R.  tau / rdiag: k entries of scratch each.
+// ldr = k) holds R.  tau / rdiag: k entries of scratch each.  With q == a the
+// thin Q is formed in place in the first k columns of a (the workspace can
+// then live in shared memory).
 template <class T>
 __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, cx<T>* rdiag, T* tau, double* red) {
   const int k = m < n ? m : n;
@@ -73,7 +75,46 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
     else if (c == i) v = rdiag[i];
     r[(long long)c * k + i] = v;
   }
-  // Q = H_0 ... H_{k-1} [I_k; 0]
+  __syncthreads();
+  if (q == a) {
+    // Q = H_0 ... H_{k-1} [I_k; 0] formed in place in the first k columns of a:
+    // for j from k-1 down to 0, apply H_j to columns j+1..k-1 (rows j..m-1;
+    // their rows <= j are zero), then replace column j, which holds v_j, by
+    // H_j e_j = e_j - tau_j v_j conj(v_j[j]).
+    for (int e = threadIdx.x; e < k * k; e += TJM_THREADS) {
+      const int i = e % k, c = e / k;
+      if (i < c) a[(long long)c * m + i] = czero<T>();
+    }
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+      const T tj = tau[j];
+      cx<T>* v = a + (long long)j * m;
+      if (tj != (T)0) {
+        for (int c = j + 1 + warp; c < k; c += TJM_WARPS) {
+          cx<T>* qc = a + (long long)c * m;
+          cx<T> s = czero<T>();
+          for (int i = j + lane; i < m; i += 32) cfma_cj(s, v[i], qc[i]);
+          s.x = warp_sum(s.x); s.y = warp_sum(s.y);
+          const cx<T> f = mk(-tj * s.x, -tj * s.y);
+          for (int i = j + lane; i < m; i += 32) cfma(qc[i], f, v[i]);
+        }
+      }
+      __syncthreads();
+      const cx<T> vj = v[j];
+      const cx<T> f = mk(-tj * vj.x, tj * vj.y);            // -tau conj(v_j)
+      __syncthreads();
+      for (int i = j + threadIdx.x; i < m; i += TJM_THREADS) {
+        const cx<T> x = v[i];
+        cx<T> y = czero<T>();
+        if (tj != (T)0) y = f * x;
+        if (i == j) y = y + mk((T)1, (T)0);
+        v[i] = y;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0] into the separate buffer q
   for (int e = threadIdx.x; e < m * k; e += TJM_THREADS) {
     const int i = e % m, c = e / m;
     q[e] = (i == c) ? mk((T)1, (T)0) : czero<T>();
@@ -101,14 +142,60 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
 // On exit: u (mm x nn) orthonormal columns sorted by decreasing singular
 // value, s[nn], v (nn x nn) with a = u diag(s) v^H.  Columns of u that belong
 // to exactly-zero singular values are completed to an orthonormal set.
-// work: nn x nn + 3 nn entries of T; iw: 2 nn ints.  Returns the sweep count.
+// vw: nn x nn rotation accumulator; sv: nn scratch values; iw: 2 nn ints.
+// Returns the sweep count.
+// One pass of classical Gram-Schmidt over the columns q[:, perm[0..n-1]]
+// (column-major, len rows), in that order, each normalised first: columns
+// that are already orthonormal to about 1e-6 come out orthonormal to working
+// precision.  Projections use compensated warp sums.  red: shared memory,
+// 2 * n + 64 doubles.
 template <class T>
-__device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T* s, cx<T>* v, cx<T>* vw, int* iw,
-                                           double* red, bool complete) {
+__device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* perm, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* h = reinterpret_cast<T*>(red + 64);
+  for (int c = 0; c < n; ++c) {
+    cx<T>* qc = q + (long long)perm[c] * len;
+    if (c > 0) {
+      for (int o = warp; o < c; o += TJM_WARPS) {
+        const cx<T>* qo = q + (long long)perm[o] * len;
+        T hx = 0, hy = 0;
+        for (int i = lane; i < len; i += 32) {
+          const cx<T> x = qo[i], y = qc[i];
+          hx = fma(x.x, y.x, fma(x.y, y.y, hx));
+          hy = fma(x.x, y.y, fma(-x.y, y.x, hy));
+        }
+        warp_sum_acc2(hx, hy);
+        if (lane == 0) { h[2 * o] = hx; h[2 * o + 1] = hy; }
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < len; i += TJM_THREADS) {
+        cx<T> a = qc[i];
+        for (int o = 0; o < c; ++o) {
+          const cx<T> x = q[(long long)perm[o] * len + i];
+          a.x -= h[2 * o] * x.x - h[2 * o + 1] * x.y;
+          a.y -= h[2 * o] * x.y + h[2 * o + 1] * x.x;
+        }
+        qc[i] = a;
+      }
+    }
+    double nr = 0.0;
+    for (int i = threadIdx.x; i < len; i += TJM_THREADS) nr += (double)norm2(qc[i]);
+    nr = blk_sum(nr, red);
+    const T f = nr > 0.0 ? (T)(1.0 / sqrt(nr)) : (T)0;
+    for (int i = threadIdx.x; i < len; i += TJM_THREADS) qc[i] = mk(qc[i].x * f, qc[i].y * f);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T* s, cx<T>* v, cx<T>* vw, T* sv,
+                                           int* iw, double* red, bool complete) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int rot_count;
   for (int e = threadIdx.x; e < nn * nn; e += TJM_THREADS) vw[e] = (e % nn == e / nn) ? mk((T)1, (T)0) : czero<T>();
-  const T tol = (T)(eps_of<T>::v * (double)mm);
+  // rotate while |a_p^H a_q| > tol sqrt(|a_p|^2 |a_q|^2); the column products
+  // are reduced in FP64 across the warp, so the test resolves well below tol
+  const T tol = (T)(sizeof(T) == 4 ? 8.0 * eps_of<T>::v : eps_of<T>::v * (double)mm);
   // Columns whose norm falls below eps * ||A||_F carry only rounding noise.
   // They are set to exactly zero and take no further part in rotations:
   // otherwise every sweep re-orthogonalises them, shrinks them by another
@@ -132,13 +219,15 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         if (p >= nn || qq >= nn) continue;
         cx<T>* ap = a + (long long)p * mm;
         cx<T>* aq = a + (long long)qq * mm;
-        T al = 0, be = 0;
-        cx<T> ga = czero<T>();
+        T al0 = 0, be0 = 0;
+        cx<T> ga0 = czero<T>();
         for (int i = lane; i < mm; i += 32) {
           const cx<T> x = ap[i], y = aq[i];
-          al += norm2(x); be += norm2(y); cfma_cj(ga, x, y);
+          al0 += norm2(x); be0 += norm2(y); cfma_cj(ga0, x, y);
         }
-        al = warp_sum(al); be = warp_sum(be); ga.x = warp_sum(ga.x); ga.y = warp_sum(ga.y);
+        warp_sum_acc4(al0, be0, ga0.x, ga0.y);
+        const T al = al0, be = be0;
+        const cx<T> ga = ga0;
         if (al <= negl || be <= negl) {
           if (al <= negl && al != (T)0) for (int i = lane; i < mm; i += 32) ap[i] = czero<T>();
           if (be <= negl && be != (T)0) for (int i = lane; i < mm; i += 32) aq[i] = czero<T>();
@@ -171,8 +260,7 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
     __syncthreads();
     if (rc == 0) break;
   }
-  // singular values, descending order (ties by index)
-  T* sv = reinterpret_cast<T*>(vw + (long long)nn * nn);
+  // singular values (unsorted in sv), descending order (ties by index)
   for (int c = warp; c < nn; c += TJM_WARPS) {
     const cx<T>* ac = a + (long long)c * mm;
     double acc = 0.0;
@@ -189,11 +277,22 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nn; e += TJM_THREADS) s[e] = sv[iw[e]];
+  const bool f32 = sizeof(T) == 4;
+  if (f32) {
+    // In FP32 the converged columns are orthogonal only to tol (about 5e-7)
+    // and the accumulated rotations drift by a similar amount; sites cut from
+    // U or V must be isometries to working precision, because every
+    // environment and transfer contraction along the chain assumes it.
+    int nz = 0;
+    for (int c = 0; c < nn; ++c) nz += sv[c] > (T)0;
+    blk_cgs_perm<T>(mm, nz, a, iw, red);
+    blk_cgs_perm<T>(nn, nn, vw, iw, red);
+  }
   for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) {
     const int i = (int)(e % mm), c = (int)(e / mm);
     const T sc = sv[iw[c]];
     const cx<T> x = a[(long long)iw[c] * mm + i];
-    u[e] = sc > (T)0 ? mk(x.x / sc, x.y / sc) : czero<T>();
+    u[e] = sc > (T)0 ? (f32 ? x : mk(x.x / sc, x.y / sc)) : czero<T>();
   }
   for (long long e = threadIdx.x; e < (long long)nn * nn; e += TJM_THREADS) {
     const int i = (int)(e % nn), c = (int)(e / nn);

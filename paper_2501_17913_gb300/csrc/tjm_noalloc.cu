@@ -51,7 +51,7 @@ svd_noalloc_kernel(int m, int n, const tjm::cx<double>* A, tjm::cx<double>* U, d
     a[e] = tr ? tjm::cvt<T>(tjm::conj(A[j * n + i])) : tjm::cvt<T>(A[i * n + j]);
   }
   __syncthreads();
-  tjm::blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, iw, red, true);
+  tjm::blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, reinterpret_cast<T*>(vw + nn * nn), iw, red, true);
   __syncthreads();
   for (int e = threadIdx.x; e < m * nn; e += TJM_THREADS) {
     const int i = e / nn, j = e % nn;

@@ -53,7 +53,7 @@ svd_test_kernel(int m, int n, const cx<double>* A, cx<double>* U, double* S, cx<
     a[e] = tr ? cvt<T>(conj(A[j * n + i])) : cvt<T>(A[i * n + j]);
   }
   __syncthreads();
-  blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, iw, red, true);
+  blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, reinterpret_cast<T*>(vw + nn * nn), iw, red, true);
   __syncthreads();
   // A = Uw S Vw^H (or its adjoint): return U (m x nn), V (n x nn) row-major
   for (int e = threadIdx.x; e < m * nn; e += TJM_THREADS) {

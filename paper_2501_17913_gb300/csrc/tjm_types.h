@@ -11,6 +11,7 @@ template <class T> struct cx;
 // observables and the output schedule (TJM Sec. "Initialization").
 struct ProbDev {
   int L, chi_max, exact, krylov_max;
+  int shift_ok;        // MPO in finite-state form: a constant can ride on the on-site channel
   int n_jumps, n_obs, n_steps, n_samples;
   double dt, trunc_eps, krylov_tol;
   const int* Dbond;                       // [L + 1] MPO bond dimensions
@@ -33,6 +34,13 @@ struct SlotStats {
   double min_margin1, min_margin2;
   double flops_contract;   // real flops of the tensor contractions (8 per complex multiply-add)
   double flops_decomp;     // real flops of the QR / SVD factorizations (Jacobi: per rotation applied)
+  unsigned long long cyc[12];   // SM cycles by phase, see tjm_phase
+};
+
+// Phases timed with clock64() by thread 0 of the CTA owning a slot.
+enum tjm_phase {
+  PH_GEMM = 0, PH_WAPPLY = 1, PH_LANCZOS = 2, PH_QR = 3, PH_SVD = 4, PH_DJ = 5, PH_MEASURE = 6, PH_TDVP = 7,
+  PH_ENVBUILD = 8, PH_EXPM = 9, PH_MATVEC = 10, PH_INIT = 11
 };
 
 // One trajectory.
@@ -44,6 +52,7 @@ struct SlotDev {
   int chi_cap;
   int flags;           // bit 0: state loaded from outside (canonicalise, rebuild envs)
                        // bit 1: U[dt] of step+1 applied, X held (phase-wise stepping)
+  double eshift;       // energy per site subtracted from H (a global phase; keeps FP32 sums small)
   void* sites;         // [L][cap_site] complex Tc
   int* chi;            // [L + 1]
   void* envL;          // [L + 1][cap_env]

@@ -135,6 +135,19 @@ def config_l1000(n_traj: int = 256) -> Workload:
                     n_traj, 0, neel(L), z_observables(L), list(range(n + 1)))
 
 
+def config_bench(n_traj: int = 256, n_steps: int = 6) -> Workload:
+    """The benchmark workload: L=1000, chi_max=64, from a seeded random MPS with every bulk bond at 64.
+
+    Same Hamiltonian and noise as config_l1000; <Z_i> recorded at every step.
+    The initial MPS is in meta['mps'] as (chi, sites).
+    """
+    L, dt = 1000, 0.1
+    wl = Workload('xxx_L1000_chi64_bench', xxx_mpo(L, 1.0, 0.5), noise(L, 0.1, 0.1), dt, n_steps, 64, 1e-10,
+                  n_traj, 0, all_zero(L), z_observables(L), list(range(n_steps + 1)))
+    wl.meta['mps'] = random_mps(L, 64, 2025)
+    return wl
+
+
 def uneven_groups(seed: int = 7, n_groups: int = 32, per_group: int = 128, dt: float = 0.05, T: float = 5.0):
     """The uneven batch: 27 groups enumerate L x chi_max x gamma, 5 more drawn at random.
 
@@ -157,6 +170,15 @@ def uneven_groups(seed: int = 7, n_groups: int = 32, per_group: int = 128, dt: f
                             dt, n, chi, 1e-10, per_group, seed, psis[0], z_observables(L), [n],
                             psi0_per_traj=psis, meta={'g': gfield, 'gamma': gam, 'first_traj': gi * per_group}))
     return out
+
+
+def uneven_group(gi: int, n_steps: int | None = None, seed: int = 7):
+    """Group gi of uneven_groups(seed), optionally cut to n_steps with every step sampled."""
+    wl = uneven_groups(seed)[gi]
+    if n_steps is not None:
+        wl.n_steps = n_steps
+        wl.sample_steps = list(range(n_steps + 1))
+    return wl
 
 
 def request_stream(seed: int = 11, n_requests: int = 200, rate: float = 20.0):

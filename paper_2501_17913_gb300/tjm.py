@@ -39,7 +39,8 @@ class tjm_state(C.Structure):
 
 class tjm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
-                ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int)]
+                ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int),
+                ("energy_shift", C.c_int)]
 
 
 class tjm_stats(C.Structure):
@@ -48,10 +49,15 @@ class tjm_stats(C.Structure):
                 ("matvec_bond", C.c_uint64), ("env_updates", C.c_uint64), ("krylov_capped", C.c_uint64),
                 ("jumps", C.c_uint64), ("min_margin_jump", C.c_double), ("min_margin_pick", C.c_double),
                 ("final_bond_sum", C.c_int64), ("final_bond_max", C.c_int64),
-                ("flops_contract", C.c_double), ("flops_decomp", C.c_double)]
+                ("flops_contract", C.c_double), ("flops_decomp", C.c_double), ("cycles", C.c_uint64 * 12)]
+
+    PHASES = ("gemm", "mpo_contract", "lanczos", "qr", "svd", "dissipate_jump", "measure", "tdvp", "env_build",
+              "krylov_expm", "matvec", "init")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cycles"}
+        d["cycles"] = {n: int(self.cycles[i]) for i, n in enumerate(self.PHASES)}
+        return d
 
 
 # (name, restype, argtypes) of every exported entry point
@@ -140,7 +146,7 @@ class Context:
     """One TJM problem (tjm_create) and the runs started on it."""
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32, krylov_max=30, krylov_tol=0.0,
-                 exact=False, device=0, max_ctas=0):
+                 exact=False, device=0, max_ctas=0, energy_shift=True):
         lib = load()
         self.lib = lib
         L = len(W)
@@ -157,6 +163,7 @@ class Context:
         lib.tjm_default_options(C.byref(opt))
         opt.precision, opt.krylov_max, opt.krylov_tol = precision, krylov_max, krylov_tol
         opt.exact_full_bond, opt.device, opt.max_ctas = int(bool(exact)), device, max_ctas
+        opt.energy_shift = int(bool(energy_shift))
         h = C.c_void_p()
         st = lib.tjm_create(C.byref(h), C.byref(mpo), js, len(jumps), float(dt), int(chi_max), float(trunc_eps),
                             C.byref(opt))
