@@ -1,0 +1,48 @@
+"""Write the stored oracle outputs used by the GPU parity tests at full size.
+
+Calls only the CPU oracle (oracle/) and the input generator; nothing here
+comes from the CUDA path.  Usage:
+
+    python tests/golden/make_golden.py l30      # L=30, chi=32: 8 sampled trajectories, all 100 steps
+    python tests/golden/make_golden.py l1000    # L=1000, chi=64 from Neel: 2 sampled trajectories, 3 steps
+    python tests/golden/make_golden.py bench    # the benchmark workload (random chi=64 MPS): trajectory 0, 1 step
+"""
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.dirname(HERE))
+
+import numpy as np  # noqa: E402
+
+from _pool import oracle_pool  # noqa: E402
+from oracle_jobs import run_traj  # noqa: E402
+
+SETS = {
+    # name: (workload factory, kwargs, sampled global trajectory ids, options)
+    "l30": ("config_l30", {}, [0, 137, 274, 411, 548, 685, 822, 959], {}),
+    "l1000": ("config_l1000", {}, [0, 201], {"n_steps": 3}),
+    "bench": ("config_bench", {}, [0], {"n_steps": 1}),
+}
+
+
+def make(name):
+    fac, kw, trajs, opts = SETS[name]
+    with oracle_pool(min(8, len(trajs))) as pool:
+        res = pool.map(run_traj, [(fac, kw, t, opts) for t in trajs])
+    vals = np.array([r[0] for r in res])
+    m1 = np.array([r[1]["min_margin1"] for r in res])
+    m2 = np.array([r[1]["min_margin2"] for r in res])
+    tm = np.array([r[1]["trunc_margin"] for r in res])
+    upto = np.array([r[1]["margin_upto"] for r in res])
+    out = os.path.join(HERE, "oracle_%s.npz" % name)
+    np.savez_compressed(out, traj=np.array(trajs), values=vals, margin_jump=m1, margin_pick=m2, trunc_margin=tm,
+                        margin_upto=upto, n_steps=opts.get("n_steps", -1))
+    print(out, vals.shape)
+
+
+if __name__ == "__main__":
+    for n in sys.argv[1:]:
+        make(n)

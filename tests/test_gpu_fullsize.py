@@ -1,0 +1,176 @@
+"""Parity at the full workload sizes, on trajectories the oracle computes one by one.
+
+The oracle values are stored by tests/golden/make_golden.py (oracle only).
+Every trajectory of a full-size run is also checked for properties that hold
+at any size: finite outputs, |<Z_i>| <= 1, status OK, bonds <= chi_max.
+
+A TJM trajectory is a chaotic map of its state: a difference of one rounding
+unit grows by roughly an order of magnitude every few steps, and once it
+exceeds the margin of a jump decision the two runs draw different jumps.
+Per-trajectory agreement with the oracle therefore holds up to a horizon that
+depends on the arithmetic (FP64 contractions and factorizations; FP32
+contractions with FP64 factorizations; everything in FP32); beyond it the
+ensembles are compared within their standard errors.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2501_17913_gb300 import inputs as I
+from paper_2501_17913_gb300 import tjm
+
+from gpu_common import lib_ready, run_gpu
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+# (last step checked, tolerance) per precision on the L=30 chain
+HORIZON = {tjm.PREC_FP64: (30, 1e-10), tjm.PREC_FP32: (20, 1e-4), tjm.PREC_FP32_DEC32: (5, 1e-4)}
+FP64_ALL_STEPS = 1e-6
+
+
+def _gold(name):
+    p = os.path.join(GOLD, "oracle_%s.npz" % name)
+    if not os.path.exists(p):
+        pytest.skip("stored oracle values %s missing (tests/golden/make_golden.py %s)" % (p, name))
+    return np.load(p)
+
+
+def _check_properties(pt, st, chi_max):
+    assert np.isfinite(pt).all()
+    assert np.abs(pt).max() <= 1.0 + 1e-5
+    assert st['failed'] == 0
+    assert st['final_bond_max'] <= chi_max
+
+
+def _compare_sampled(pt, g, tol, margin, last_step=None):
+    """Sampled trajectories pt[traj] against the stored oracle values up to last_step."""
+    ok = 0
+    sl = slice(None) if last_step is None else slice(0, last_step + 1)
+    for k, t in enumerate(g['traj']):
+        # the smallest margin of the decisions taken up to the last compared step
+        if g['margin_upto'][k][-1 if last_step is None else last_step] < margin:
+            continue
+        err = float(np.abs(pt[t][sl] - g['values'][k][sl]).max())
+        assert err < tol, (int(t), err)
+        ok += 1
+    assert ok >= len(g['traj']) - 2
+    return ok
+
+
+def _sampled_runs(wl, g, prec):
+    """The sampled L=30 trajectories, each its own run, all in one launch."""
+    lib_ready()
+    ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=prec)
+    runs = [ctx.prepare(np.array(wl.psi0), 1, wl.seed, wl.observables, wl.times, first_traj=int(t))
+            for t in g['traj']]
+    tjm.group_advance([(ctx, r) for r in runs], wl.n_steps + 1)
+    pt = {}
+    for t, r in zip(g['traj'], runs):
+        pt[int(t)] = ctx.result(r)[2][0]
+    ctx.close()
+    return pt
+
+
+@pytest.mark.parametrize("prec", [tjm.PREC_FP64, tjm.PREC_FP32, tjm.PREC_FP32_DEC32])
+def test_l30_sampled_trajectories_to_horizon(prec):
+    """L=30, chi_max=32, 100 steps: the sampled trajectories against the oracle up to the precision's horizon."""
+    g = _gold("l30")
+    wl = I.config_l30()
+    pt = _sampled_runs(wl, g, prec)
+    last, tol = HORIZON[prec]
+    _compare_sampled(pt, g, tol, 1e-4, last_step=last)
+    if prec == tjm.PREC_FP64:
+        _compare_sampled(pt, g, FP64_ALL_STEPS, 1e-4)
+
+
+@pytest.mark.parametrize("prec", [tjm.PREC_FP32_DEC32, tjm.PREC_FP32])
+def test_l30_1024_trajectories_ensemble_fp32_vs_fp64(prec):
+    """All 1024 L=30 trajectories for 100 steps: properties of every trajectory, the sampled ones to the
+    horizon, and the FP32 ensemble mean within 3 standard errors of the FP64 ensemble mean."""
+    g = _gold("l30")
+    wl = I.config_l30()
+    pt, mean, sem, st, _, ctx = run_gpu(wl, prec)
+    ctx.close()
+    _check_properties(pt, st, wl.chi_max)
+    last, tol = HORIZON[prec]
+    _compare_sampled(pt, g, tol, 1e-4, last_step=last)
+    pt64, mean64, sem64, st64, _, ctx = run_gpu(wl, tjm.PREC_FP64)
+    ctx.close()
+    _check_properties(pt64, st64, wl.chi_max)
+    se = np.sqrt(sem ** 2 + sem64 ** 2)
+    se = np.maximum(se, 1e-4)
+    z = np.abs(mean - mean64) / se
+    assert (z <= 3.0).mean() >= 0.99, (z > 3.0).mean()
+    assert z.max() <= 5.0, z.max()
+
+
+@pytest.mark.parametrize("prec,tol", [(tjm.PREC_FP64, 1e-10), (tjm.PREC_FP32, 1e-4), (tjm.PREC_FP32_DEC32, 2e-4)])
+def test_l1000_neel_first_steps(prec, tol):
+    """L=1000, chi_max=64, 256 trajectories from Neel, 3 steps: sampled trajectories against the oracle."""
+    g = _gold("l1000")
+    wl = I.config_l1000()
+    pt, mean, sem, st, _, ctx = run_gpu(wl, prec, n_steps=int(g['n_steps']))
+    ctx.close()
+    _check_properties(pt, st, wl.chi_max)
+    _compare_sampled(pt, g, tol, 1e-4)
+
+
+@pytest.mark.parametrize("prec,tol", [(tjm.PREC_FP32, 1e-4), (tjm.PREC_FP32_DEC32, 1e-4)])
+def test_bench_workload_one_step(prec, tol):
+    """The benchmark launch: L=1000, chi=64-saturated random MPS, 256 trajectories, one step."""
+    g = _gold("bench")
+    wl = I.config_bench()
+    pt, mean, sem, st, _, ctx = run_gpu(wl, prec, n_steps=1, psi=wl.meta['mps'])
+    ctx.close()
+    _check_properties(pt, st, wl.chi_max)
+    _compare_sampled(pt, g, tol, 1e-5)
+
+
+def test_uneven_batch_one_launch_matches_alone_and_oracle():
+    """4096 trajectories over 32 groups (L in {50,100,200}, chi_max in {16,32,64}, gamma in {0.01,0.1,1}),
+    all in one persistent launch, 3 steps: every group's results equal the same group run alone, and
+    sampled trajectories match the oracle."""
+    from _pool import oracle_pool
+    from oracle_jobs import run_traj
+    lib_ready()
+    groups = I.uneven_groups()
+    n_steps = 3
+    ctxs, runs = [], []
+    for wl in groups:
+        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DEC32)
+        times = [s * wl.dt for s in range(n_steps + 1)]
+        r = ctx.prepare(np.array(wl.psi0_per_traj), wl.n_traj, wl.seed, wl.observables, times,
+                        first_traj=wl.meta['first_traj'])
+        ctxs.append(ctx)
+        runs.append(r)
+    tjm.group_advance(list(zip(ctxs, runs)), n_steps + 1)
+    mixed = []
+    for ctx, r, wl in zip(ctxs, runs, groups):
+        pt = ctx.result(r)[2]
+        st = ctx.stats(r)
+        _check_properties(pt, st, wl.chi_max)
+        mixed.append(pt)
+    # alone: two groups with different L and chi, each in its own launch
+    for gi in (0, 31):
+        wl = groups[gi]
+        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DEC32)
+        times = [s * wl.dt for s in range(n_steps + 1)]
+        r = ctx.run(np.array(wl.psi0_per_traj), wl.n_traj, wl.seed, wl.observables, times,
+                    first_traj=wl.meta['first_traj'])
+        alone = ctx.result(r)[2]
+        assert np.array_equal(alone, mixed[gi]), gi
+        ctx.close()
+    # oracle: one trajectory of each of a few groups (cheap: short times, product start)
+    picks = [(0, 5), (13, 77), (26, 127)]
+    with oracle_pool(len(picks)) as pool:
+        res = pool.map(run_traj, [('uneven_group', {'gi': gi, 'n_steps': n_steps}, k, {'n_steps': n_steps,
+                                                                   'traj_offset': groups[gi].meta['first_traj']})
+                                  for gi, k in picks])
+    for (gi, k), (v, stt) in zip(picks, res):
+        if min(stt['min_margin1'], stt['min_margin2']) < 1e-5:
+            continue
+        assert np.abs(mixed[gi][k] - v).max() < 1e-4, (gi, k)
+    for ctx in ctxs:
+        ctx.close()

@@ -77,12 +77,25 @@ def test_small_chain_fp64_all_trajectories_and_lindblad():
 
 @pytest.mark.parametrize("prec", [tjm.PREC_FP32, tjm.PREC_FP32_DEC32])
 def test_small_chain_fp32_paths(prec):
+    """L=6, 64 trajectories, FP32 contractions: per trajectory within 1e-4 of the FP64 oracle for the
+    first 30 of 50 steps (rounding differences grow along a trajectory; the margins counted are those
+    of the decisions up to step 30), and the ensemble within the 3-SE rule of the oracle's at all steps."""
+    horizon = 30
     wl = I.config_small_fp64(64)
     pt, mean, sem, st, _, _ = run_gpu(wl, prec)
     res = _oracle('config_small_fp64', {'n_traj': 64}, range(64), {})
-    ok, skipped, worst = _compare(pt, res, 1e-4, 1e-5)
+    ok, worst = 0, 0.0
+    for g, (v, so) in zip(pt, res):
+        if so['margin_upto'][horizon] < 1e-5:
+            continue
+        worst = max(worst, float(np.abs(g[:horizon + 1] - v[:horizon + 1]).max()))
+        ok += 1
     assert worst < 1e-4, worst
     assert ok >= 60
+    om = np.array([v for v, _ in res])
+    se = np.sqrt(sem ** 2 + (om.std(axis=0, ddof=1) / np.sqrt(len(om))) ** 2)
+    z = np.abs(mean - om.mean(axis=0))[1:] / np.maximum(se[1:], 1e-4)
+    assert np.mean(z < 3) >= 0.99 and z.max() < 5
 
 
 def test_edge_cases_fp64():
