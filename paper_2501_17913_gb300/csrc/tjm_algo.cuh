@@ -224,21 +224,46 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       else if (kind == 2) heff2(c, l, chl, chr, vk, c.w);
       else heff0(c, l, chl, chr, vk, c.w);
     });
-    // Orthogonalise w = H v_k against v_0..v_k by classical Gram-Schmidt,
-    // twice (the three-term recurrence is part of the projection; h_k = alpha_k).
-    // Each projection reads w once per chunk of 8 basis vectors to form all
-    // coefficients, then once more to subtract them while accumulating the new
-    // ||w||^2.  Coefficients are reduced in FP64.
+    // Three-term recurrence, then one classical Gram-Schmidt pass against
+    // the whole basis (the recurrence acts as the first orthogonalisation
+    // pass).  (1) w -= beta_{k-1} v_{k-1} while forming alpha = <v_k, w>;
+    // (2) w -= alpha v_k while forming all coefficients h_j = <v_j, w> in
+    // chunks of 8 basis vectors; (3) w -= sum_j h_j v_j while forming ||w||^2.
+    // Coefficients are reduced in FP64; alpha_k = alpha + Re h_k.
     const int nb = k + 1;
-    double wn2 = 0.0, al_k = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
+    const cx<Tc>* vk0 = c.krylov + (long long)k * n;
+    double al_k;
+    {
+      const cx<Tc>* vkm = c.krylov + (long long)(k > 0 ? k - 1 : 0) * n;
+      const Tc bm = k > 0 ? (Tc)beta[k - 1] : (Tc)0;
+      Tc ax = 0;
+      for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
+        cx<Tc> t = c.w[i];
+        if (k > 0) { t.x -= bm * vkm[i].x; t.y -= bm * vkm[i].y; }
+        c.w[i] = t;
+        const cx<Tc> v = vk0[i];
+        ax = fma(v.x, t.x, fma(v.y, t.y, ax));
+      }
+      // <v_k, w> is real for Hermitian H up to rounding; what is left of it
+      // is removed with h_k below
+      al_k = blk_sum((double)ax, c.red);
+      __syncthreads();   // red is reused for the coefficients
+    }
+    {
+      const Tc a0 = (Tc)al_k;
       for (int j0 = 0; j0 < nb; j0 += 8) {
         const int jn = nb - j0 < 8 ? nb - j0 : 8;
         cx<Tc> acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = czero<Tc>();
         for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-          const cx<Tc> wi = c.w[i];
+          cx<Tc> wi = c.w[i];
+          if (j0 == 0) {   // each thread updates, then rereads, only its own entries
+            const cx<Tc> v = vk0[i];
+            wi.x -= a0 * v.x;
+            wi.y -= a0 * v.y;
+            c.w[i] = wi;
+          }
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             if (q < jn) cfma_cj(acc[q], c.krylov[(long long)(j0 + q) * n + i], wi);
@@ -254,8 +279,11 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
           }
         }
       }
-      blk_sums_finish(2 * nb, c.red, hh);
-      al_k += hh[2 * k];
+    }
+    blk_sums_finish(2 * nb, c.red, hh);
+    al_k += hh[2 * k];
+    double wn2;
+    {
       // coefficients converted once (FP64 -> working precision), not per element
       cx<Tc>* hw = reinterpret_cast<cx<Tc>*>(c.red);
       for (int j = threadIdx.x; j < nb; j += TJM_THREADS) hw[j] = mk((Tc)hh[2 * j], (Tc)hh[2 * j + 1]);

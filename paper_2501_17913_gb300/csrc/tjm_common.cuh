@@ -64,16 +64,6 @@ __device__ __forceinline__ f2s df_add(f2s a, f2s b) {
   const float h = s + e;
   return {h, e - (h - s)};
 }
-__device__ __forceinline__ void warp_sum_df4(float& v0, float& v1, float& v2, float& v3) {
-  f2s a = {v0, 0.f}, b = {v1, 0.f}, c = {v2, 0.f}, d = {v3, 0.f};
-  for (int o = 16; o > 0; o >>= 1) {
-    a = df_add(a, {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
-    b = df_add(b, {__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o)});
-    c = df_add(c, {__shfl_xor_sync(0xffffffffu, c.hi, o), __shfl_xor_sync(0xffffffffu, c.lo, o)});
-    d = df_add(d, {__shfl_xor_sync(0xffffffffu, d.hi, o), __shfl_xor_sync(0xffffffffu, d.lo, o)});
-  }
-  v0 = a.hi + a.lo; v1 = b.hi + b.lo; v2 = c.hi + c.lo; v3 = d.hi + d.lo;
-}
 __device__ __forceinline__ void warp_sum_df2(float& v0, float& v1) {
   f2s a = {v0, 0.f}, b = {v1, 0.f};
   for (int o = 16; o > 0; o >>= 1) {
@@ -84,14 +74,27 @@ __device__ __forceinline__ void warp_sum_df2(float& v0, float& v1) {
 }
 // Accurate warp sums in the factorization precision: FP64 shuffles for
 // double, compensated FP32 for float.
-__device__ __forceinline__ void warp_sum_acc4(double& v0, double& v1, double& v2, double& v3) {
-  v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2); v3 = warp_sum(v3);
-}
-__device__ __forceinline__ void warp_sum_acc4(float& v0, float& v1, float& v2, float& v3) {
-  warp_sum_df4(v0, v1, v2, v3);
-}
 __device__ __forceinline__ void warp_sum_acc2(double& v0, double& v1) { v0 = warp_sum(v0); v1 = warp_sum(v1); }
 __device__ __forceinline__ void warp_sum_acc2(float& v0, float& v1) { warp_sum_df2(v0, v1); }
+
+// Sums over an aligned group of 8 lanes (mask m = exactly those lanes).
+template <class T> __device__ __forceinline__ T grp8_sum(T v, unsigned m) {
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+  return v;
+}
+__device__ __forceinline__ void grp8_sum_acc2(double& v0, double& v1, unsigned m) {
+  v0 = grp8_sum(v0, m);
+  v1 = grp8_sum(v1, m);
+}
+// compensated (see warp_sum_df2) for FP32
+__device__ __forceinline__ void grp8_sum_acc2(float& v0, float& v1, unsigned m) {
+  f2s a = {v0, 0.f}, b = {v1, 0.f};
+  for (int o = 4; o > 0; o >>= 1) {
+    a = df_add(a, {__shfl_xor_sync(m, a.hi, o), __shfl_xor_sync(m, a.lo, o)});
+    b = df_add(b, {__shfl_xor_sync(m, b.hi, o), __shfl_xor_sync(m, b.lo, o)});
+  }
+  v0 = a.hi + a.lo; v1 = b.hi + b.lo;
+}
 
 __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -18,6 +18,36 @@ template <> struct eps_of<float> { static constexpr double v = 1.192092895507812
 template <> struct eps_of<double> { static constexpr double v = 2.220446049250313e-16; };
 
 // ------------------------------------------------------------------ QR
+// x[:, c] <- (I - tau v v^H) x[:, c] for columns c0 <= c < c1 of x (column-major,
+// leading dimension m), acting on rows j..m-1 where v lives.  One aligned
+// group of 8 lanes per column, so a warp works on four columns at once and
+// each dot product needs only a 3-step shuffle reduction; the groups of a
+// warp start their walk down the column 8 rows apart, so their shared-memory
+// reads fall in different banks.
+template <class T>
+__device__ __forceinline__ void grp_reflect(int m, int j, const cx<T>* v, T tj, cx<T>* x, int c0, int c1) {
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  const unsigned gmask = 0xffu << ((threadIdx.x & 31) & 24);
+  const int len = m - j;
+  if (len <= 0) return;
+  const int i0 = j + (gl + 8 * (grp & 3)) % len;
+  for (int c = c0 + grp; c < c1; c += TJM_THREADS / 8) {
+    cx<T>* xc = x + (long long)c * m;
+    cx<T> s = czero<T>();
+    for (int t = gl, i = i0; t < len; t += 8) {
+      cfma_cj(s, v[i], xc[i]);
+      i += 8; if (i >= m) i -= len;
+    }
+    s.x = grp8_sum(s.x, gmask);
+    s.y = grp8_sum(s.y, gmask);
+    const cx<T> f = mk(-tj * s.x, -tj * s.y);
+    for (int t = gl, i = i0; t < len; t += 8) {
+      cfma(xc[i], f, v[i]);
+      i += 8; if (i >= m) i -= len;
+    }
+  }
+}
+
 // a: m x n column-major (lda = m), factorised in place.  k = min(m, n).
 // On exit q (m x k, column-major) holds the thin Q, r (k x n, column-major,
 // ldr = k) holds R.  tau / rdiag: k entries of scratch each.  With q == a the
@@ -26,7 +56,6 @@ template <> struct eps_of<double> { static constexpr double v = 2.22044604925031
 template <class T>
 __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, cx<T>* rdiag, T* tau, double* red) {
   const int k = m < n ? m : n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // A remaining column below eps * ||A||_F is rounding noise: no reflector is
   // built from it (its 1/(v^H v) would overflow in FP32) and it is left as is,
   // a backward error of at most eps * ||A||_F.
@@ -55,16 +84,7 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
     }
     __syncthreads();
     const T tj = tau[j];
-    if (tj != (T)0) {
-      for (int c = j + 1 + warp; c < n; c += TJM_WARPS) {
-        cx<T>* cc = a + (long long)c * m;
-        cx<T> s = czero<T>();
-        for (int i = j + lane; i < m; i += 32) cfma_cj(s, col[i], cc[i]);
-        s.x = warp_sum(s.x); s.y = warp_sum(s.y);
-        const cx<T> f = mk(-tj * s.x, -tj * s.y);
-        for (int i = j + lane; i < m; i += 32) cfma(cc[i], f, col[i]);
-      }
-    }
+    if (tj != (T)0) grp_reflect<T>(m, j, col, tj, a, j + 1, n);
     __syncthreads();
   }
   // R (k x n)
@@ -89,16 +109,7 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
     for (int j = k - 1; j >= 0; --j) {
       const T tj = tau[j];
       cx<T>* v = a + (long long)j * m;
-      if (tj != (T)0) {
-        for (int c = j + 1 + warp; c < k; c += TJM_WARPS) {
-          cx<T>* qc = a + (long long)c * m;
-          cx<T> s = czero<T>();
-          for (int i = j + lane; i < m; i += 32) cfma_cj(s, v[i], qc[i]);
-          s.x = warp_sum(s.x); s.y = warp_sum(s.y);
-          const cx<T> f = mk(-tj * s.x, -tj * s.y);
-          for (int i = j + lane; i < m; i += 32) cfma(qc[i], f, v[i]);
-        }
-      }
+      if (tj != (T)0) grp_reflect<T>(m, j, v, tj, a, j + 1, k);
       __syncthreads();
       const cx<T> vj = v[j];
       const cx<T> f = mk(-tj * vj.x, tj * vj.y);            // -tau conj(v_j)
@@ -122,28 +133,11 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
     const T tj = tau[j];
-    if (tj != (T)0) {
-      const cx<T>* v = a + (long long)j * m;
-      for (int c = j + warp; c < k; c += TJM_WARPS) {
-        cx<T>* qc = q + (long long)c * m;
-        cx<T> s = czero<T>();
-        for (int i = j + lane; i < m; i += 32) cfma_cj(s, v[i], qc[i]);
-        s.x = warp_sum(s.x); s.y = warp_sum(s.y);
-        const cx<T> f = mk(-tj * s.x, -tj * s.y);
-        for (int i = j + lane; i < m; i += 32) cfma(qc[i], f, v[i]);
-      }
-    }
+    if (tj != (T)0) grp_reflect<T>(m, j, a + (long long)j * m, tj, q, j, k);
     __syncthreads();
   }
 }
 
-// ------------------------------------------------------------------ Jacobi SVD
-// a: mm x nn column-major with mm >= nn (the caller transposes when needed).
-// On exit: u (mm x nn) orthonormal columns sorted by decreasing singular
-// value, s[nn], v (nn x nn) with a = u diag(s) v^H.  Columns of u that belong
-// to exactly-zero singular values are completed to an orthonormal set.
-// vw: nn x nn rotation accumulator; sv: nn scratch values; iw: 2 nn ints.
-// Returns the sweep count.
 // One pass of classical Gram-Schmidt over the columns q[:, perm[0..n-1]]
 // (column-major, len rows), in that order, each normalised first: columns
 // that are already orthonormal to about 1e-6 come out orthonormal to working
@@ -151,21 +145,23 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
 // 2 * n + 64 doubles.
 template <class T>
 __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* perm, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  const unsigned gmask = 0xffu << ((threadIdx.x & 31) & 24);
   T* h = reinterpret_cast<T*>(red + 64);
   for (int c = 0; c < n; ++c) {
     cx<T>* qc = q + (long long)perm[c] * len;
     if (c > 0) {
-      for (int o = warp; o < c; o += TJM_WARPS) {
+      // one aligned group of 8 lanes per projection
+      for (int o = grp; o < c; o += TJM_THREADS / 8) {
         const cx<T>* qo = q + (long long)perm[o] * len;
         T hx = 0, hy = 0;
-        for (int i = lane; i < len; i += 32) {
+        for (int i = gl; i < len; i += 8) {
           const cx<T> x = qo[i], y = qc[i];
           hx = fma(x.x, y.x, fma(x.y, y.y, hx));
           hy = fma(x.x, y.y, fma(-x.y, y.x, hy));
         }
-        warp_sum_acc2(hx, hy);
-        if (lane == 0) { h[2 * o] = hx; h[2 * o + 1] = hy; }
+        grp8_sum_acc2(hx, hy, gmask);
+        if (gl == 0) { h[2 * o] = hx; h[2 * o + 1] = hy; }
       }
       __syncthreads();
       for (int i = threadIdx.x; i < len; i += TJM_THREADS) {
@@ -187,14 +183,21 @@ __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* p
   }
 }
 
+// ------------------------------------------------------------------ Jacobi SVD
+// a: mm x nn column-major with mm >= nn (the caller transposes when needed).
+// On exit: u (mm x nn) orthonormal columns sorted by decreasing singular
+// value, s[nn], v (nn x nn) with a = u diag(s) v^H.  Columns of u that belong
+// to exactly-zero singular values are completed to an orthonormal set.
+// vw: nn x nn rotation accumulator; sv: nn scratch values; iw: 2 nn ints.
+// Returns the sweep count.
 template <class T>
 __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T* s, cx<T>* v, cx<T>* vw, T* sv,
                                            int* iw, double* red, bool complete) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ int rot_count;
   for (int e = threadIdx.x; e < nn * nn; e += TJM_THREADS) vw[e] = (e % nn == e / nn) ? mk((T)1, (T)0) : czero<T>();
-  // rotate while |a_p^H a_q| > tol sqrt(|a_p|^2 |a_q|^2); the column products
-  // are reduced in FP64 across the warp, so the test resolves well below tol
+  // rotate while |a_p^H a_q| > tol sqrt(|a_p|^2 |a_q|^2); the products are
+  // reduced with compensation (FP32) or in FP64, so the test resolves below tol
   const T tol = (T)(sizeof(T) == 4 ? 8.0 * eps_of<T>::v : eps_of<T>::v * (double)mm);
   // Columns whose norm falls below eps * ||A||_F carry only rounding noise.
   // They are set to exactly zero and take no further part in rotations:
@@ -206,12 +209,21 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
   fro2 = blk_sum(fro2, red);
   const T negl = (T)(eps_of<T>::v * eps_of<T>::v * fro2);
   const int ne = nn + (nn & 1);
+  // Each pair of columns is handled by an aligned group of 8 lanes (4 pairs
+  // per warp): the per-pair cross-lane reduction is then 3 shuffle steps
+  // instead of 5, over a quarter of the lanes.  Groups of one warp start
+  // their column walk 8 elements apart, so their shared-memory reads fall in
+  // different banks.
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  const unsigned gmask = 0xffu << (lane & 24);
+  const int off = 8 * (grp & 3);
+  const int ia0 = (gl + off) % mm, iv0 = (gl + off) % nn;
   int sweep = 0;
   for (; sweep < 40 && nn > 1; ++sweep) {
     if (threadIdx.x == 0) rot_count = 0;
     __syncthreads();
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
-      for (int pr = warp; pr < ne / 2; pr += TJM_WARPS) {
+      for (int pr = grp; pr < ne / 2; pr += TJM_THREADS / 8) {
         // circle-method pairing: position 0 fixed, the others rotate
         const int pa = pr, pb = ne - 1 - pr;
         const int p = pa == 0 ? 0 : ((pa - 1 + rnd) % (ne - 1)) + 1;
@@ -221,16 +233,19 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         cx<T>* aq = a + (long long)qq * mm;
         T al0 = 0, be0 = 0;
         cx<T> ga0 = czero<T>();
-        for (int i = lane; i < mm; i += 32) {
+        for (int r = gl, i = ia0; r < mm; r += 8) {
           const cx<T> x = ap[i], y = aq[i];
           al0 += norm2(x); be0 += norm2(y); cfma_cj(ga0, x, y);
+          i += 8; if (i >= mm) i -= mm;
         }
-        warp_sum_acc4(al0, be0, ga0.x, ga0.y);
-        const T al = al0, be = be0;
+        // column norms add positive terms (no cancellation); the product is
+        // reduced with compensation in FP32
+        const T al = grp8_sum(al0, gmask), be = grp8_sum(be0, gmask);
+        grp8_sum_acc2(ga0.x, ga0.y, gmask);
         const cx<T> ga = ga0;
         if (al <= negl || be <= negl) {
-          if (al <= negl && al != (T)0) for (int i = lane; i < mm; i += 32) ap[i] = czero<T>();
-          if (be <= negl && be != (T)0) for (int i = lane; i < mm; i += 32) aq[i] = czero<T>();
+          if (al <= negl && al != (T)0) for (int i = gl; i < mm; i += 8) ap[i] = czero<T>();
+          if (be <= negl && be != (T)0) for (int i = gl; i < mm; i += 8) aq[i] = czero<T>();
           continue;
         }
         const T ag = sqrt(norm2(ga));
@@ -240,19 +255,21 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         const T c = (T)1 / sqrt((T)1 + t * t), sn = c * t;
         const cx<T> ph = mk(ga.x / ag, -ga.y / ag);           // e^{-i phi}
         // [a_p, a_q] <- [a_p, a_q] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]
-        for (int i = lane; i < mm; i += 32) {
+        for (int r = gl, i = ia0; r < mm; r += 8) {
           const cx<T> x = ap[i], y = ph * aq[i];
           ap[i] = c * x - sn * y;
           aq[i] = sn * x + c * y;
+          i += 8; if (i >= mm) i -= mm;
         }
         cx<T>* vp = vw + (long long)p * nn;
         cx<T>* vq = vw + (long long)qq * nn;
-        for (int i = lane; i < nn; i += 32) {
+        for (int r = gl, i = iv0; r < nn; r += 8) {
           const cx<T> x = vp[i], y = ph * vq[i];
           vp[i] = c * x - sn * y;
           vq[i] = sn * x + c * y;
+          i += 8; if (i >= nn) i -= nn;
         }
-        if (lane == 0) atomicAdd(&rot_count, 1);
+        if (gl == 0) atomicAdd(&rot_count, 1);
       }
       __syncthreads();
     }
