@@ -115,6 +115,23 @@ __device__ __forceinline__ double blk_sum(double v, double* red) {
   return s;
 }
 
+// As blk_sum in FP32, for sums of non-negative terms (no cancellation, so FP32
+// is accurate to a few ulps and no FP64 instruction is needed).
+__device__ __forceinline__ float blk_sumf(float v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* rf = reinterpret_cast<float*>(red);
+  __syncthreads();
+  if (lane == 0) rf[w] = v;
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < TJM_WARPS; ++i) s += rf[i];
+  return s;
+}
+__device__ __forceinline__ double blk_sum_pos(double v, double* red) { return blk_sum(v, red); }
+__device__ __forceinline__ float blk_sum_pos(float v, double* red) { return blk_sumf(v, red); }
+
 // Several sums at once: partial[j] for j < n (n <= 64); results land in out[j]
 // (shared memory) after the call.  red needs n * TJM_WARPS doubles.
 __device__ __forceinline__ void blk_sums_finish(int n, double* red, double* out) {

@@ -24,8 +24,11 @@ template <> struct eps_of<double> { static constexpr double v = 2.22044604925031
 // each dot product needs only a 3-step shuffle reduction; the groups of a
 // warp start their walk down the column 8 rows apart, so their shared-memory
 // reads fall in different banks.
+// If nrm is given, the group that owns column c0 also stores there the
+// squared norm of that column's rows j+1..m-1 after the update.
 template <class T>
-__device__ __forceinline__ void grp_reflect(int m, int j, const cx<T>* v, T tj, cx<T>* x, int c0, int c1) {
+__device__ __forceinline__ void grp_reflect(int m, int j, const cx<T>* v, T tj, cx<T>* x, int c0, int c1,
+                                            T* nrm = nullptr) {
   const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
   const unsigned gmask = 0xffu << ((threadIdx.x & 31) & 24);
   const int len = m - j;
@@ -41,9 +44,17 @@ __device__ __forceinline__ void grp_reflect(int m, int j, const cx<T>* v, T tj, 
     s.x = grp8_sum(s.x, gmask);
     s.y = grp8_sum(s.y, gmask);
     const cx<T> f = mk(-tj * s.x, -tj * s.y);
+    T q2 = 0;
     for (int t = gl, i = i0; t < len; t += 8) {
-      cfma(xc[i], f, v[i]);
+      cx<T> y = xc[i];
+      cfma(y, f, v[i]);
+      xc[i] = y;
+      if (i > j) q2 += norm2(y);
       i += 8; if (i >= m) i -= len;
+    }
+    if (nrm && c == c0) {
+      q2 = grp8_sum(q2, gmask);
+      if (gl == 0) *nrm = q2;
     }
   }
 }
@@ -62,31 +73,52 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
   double fro2 = 0.0;
   for (long long e = threadIdx.x; e < (long long)m * n; e += TJM_THREADS) fro2 += (double)norm2(a[e]);
   fro2 = blk_sum(fro2, red);
-  const double negl = eps_of<T>::v * eps_of<T>::v * fro2;
+  const T negl = (T)(eps_of<T>::v * eps_of<T>::v * fro2);
+  // cn[j & 1]: squared norm of rows j..m-1 of the pivot column j.  It is
+  // produced by the group that applies reflector j-1 to column j, so no
+  // block-wide reduction stands between two reflectors.
+  T* cn = reinterpret_cast<T*>(red + 256);
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  const unsigned gmask = 0xffu << ((threadIdx.x & 31) & 24);
+  if (threadIdx.x < 8) {
+    T s2 = 0;
+    for (int i = threadIdx.x; i < m; i += 8) s2 += norm2(a[i]);
+    s2 = grp8_sum(s2, 0xffu);
+    if (threadIdx.x == 0) cn[0] = s2;
+  }
+  __syncthreads();
   for (int j = 0; j < k; ++j) {
     cx<T>* col = a + (long long)j * m;
-    double s2 = 0.0;
-    for (int i = j + threadIdx.x; i < m; i += TJM_THREADS) s2 += (double)norm2(col[i]);
-    s2 = blk_sum(s2, red);
     if (threadIdx.x == 0) {
       const cx<T> al = col[j];
-      const double sig = sqrt(s2);
+      const T s2 = cn[j & 1];
       if (s2 <= negl) {
         tau[j] = (T)0; rdiag[j] = al;
       } else {
-        const double aa = sqrt((double)norm2(al));
-        const double px = aa > 0 ? (double)al.x / aa : 1.0, py = aa > 0 ? (double)al.y / aa : 0.0;
-        const cx<T> be = mk((T)(-px * sig), (T)(-py * sig));
+        const T sig = sqrt(s2);
+        const T aa = sqrt(norm2(al));
+        const T px = aa > (T)0 ? al.x / aa : (T)1, py = aa > (T)0 ? al.y / aa : (T)0;
+        const cx<T> be = mk(-px * sig, -py * sig);
         col[j] = al - be;
-        tau[j] = (T)(1.0 / (s2 + aa * sig));          // 2 / (v^H v)
+        tau[j] = (T)1 / (s2 + aa * sig);          // 2 / (v^H v)
         rdiag[j] = be;
       }
     }
     __syncthreads();
     const T tj = tau[j];
-    if (tj != (T)0) grp_reflect<T>(m, j, col, tj, a, j + 1, n);
+    T* nx = j + 1 < k ? &cn[(j + 1) & 1] : nullptr;
+    if (tj != (T)0) {
+      grp_reflect<T>(m, j, col, tj, a, j + 1, n, nx);
+    } else if (nx && grp == 0) {
+      const cx<T>* xc = a + (long long)(j + 1) * m;
+      T s2 = 0;
+      for (int i = j + 1 + gl; i < m; i += 8) s2 += norm2(xc[i]);
+      s2 = grp8_sum(s2, gmask);
+      if (gl == 0) *nx = s2;
+    }
     __syncthreads();
   }
+  __syncthreads();
   // R (k x n)
   for (int e = threadIdx.x; e < k * n; e += TJM_THREADS) {
     const int i = e % k, c = e / k;
@@ -109,9 +141,8 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
     for (int j = k - 1; j >= 0; --j) {
       const T tj = tau[j];
       cx<T>* v = a + (long long)j * m;
+      const cx<T> vj = v[j];              // column j is rewritten below, after the barrier
       if (tj != (T)0) grp_reflect<T>(m, j, v, tj, a, j + 1, k);
-      __syncthreads();
-      const cx<T> vj = v[j];
       const cx<T> f = mk(-tj * vj.x, tj * vj.y);            // -tau conj(v_j)
       __syncthreads();
       for (int i = j + threadIdx.x; i < m; i += TJM_THREADS) {
@@ -174,10 +205,10 @@ __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* p
         qc[i] = a;
       }
     }
-    double nr = 0.0;
-    for (int i = threadIdx.x; i < len; i += TJM_THREADS) nr += (double)norm2(qc[i]);
-    nr = blk_sum(nr, red);
-    const T f = nr > 0.0 ? (T)(1.0 / sqrt(nr)) : (T)0;
+    T nr = 0;
+    for (int i = threadIdx.x; i < len; i += TJM_THREADS) nr += norm2(qc[i]);
+    nr = blk_sum_pos(nr, red);
+    const T f = nr > (T)0 ? (T)1 / sqrt(nr) : (T)0;
     for (int i = threadIdx.x; i < len; i += TJM_THREADS) qc[i] = mk(qc[i].x * f, qc[i].y * f);
     __syncthreads();
   }
