@@ -199,6 +199,15 @@ tjm_status tjm_run_get_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int* st
 tjm_status tjm_run_set_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int step, const int* chi,
                              const double* data);
 
+/* tjm_run_set_tile_rule -- GEMM tile rule for this run's later launches:
+ * 0 (default) 64 x 64 output tiles everywhere; 1 32 x 32 tiles for products
+ * with an output dimension <= 32 (small bonds, chain ends).  Both compute the
+ * same contractions (results differ only by summation order).  The choice is
+ * made by the host autotuner (paper_2501_17913_gb300/autotune.py) from timed
+ * launches; it is not from the paper.  Blocks until the setting is on the
+ * device; TJM_EINVAL for another rule or an unknown run. */
+tjm_status tjm_run_set_tile_rule(tjm_ctx* ctx, int64_t run_id, int rule);
+
 /* tjm_run_status -- per-trajectory status, [n_traj] (TJM_OK or TJM_ENUMERIC;
  * a failed trajectory stops advancing and keeps its last good outputs). */
 tjm_status tjm_run_status(tjm_ctx* ctx, int64_t run_id, int* status);

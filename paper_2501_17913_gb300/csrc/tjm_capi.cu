@@ -8,6 +8,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -905,6 +906,19 @@ tjm_status tjm_run_status(tjm_ctx* ctx, int64_t run_id, int* status) {
   tjm_status st = fetch_slots(ctx, R, hs);
   if (st) return st;
   for (size_t t = 0; t < hs.size(); ++t) status[t] = hs[t].status;
+  return TJM_OK;
+}
+
+tjm_status tjm_run_set_tile_rule(tjm_ctx* ctx, int64_t run_id, int rule) {
+  if (!ctx) return TJM_EINVAL;
+  Run* R = find_run(ctx, run_id);
+  if (!R) return fail(ctx, TJM_EINVAL, "unknown run");
+  if (rule < 0 || rule > 1) return fail(ctx, TJM_EINVAL, "tile rule must be 0 or 1");
+  cudaSetDevice(ctx->device);
+  // stream-ordered: launches issued after this call see the new rule
+  TJM_CU(cudaMemcpyAsync(reinterpret_cast<char*>(R->prob) + offsetof(tjm::ProbDev, gemm_rule), &rule, sizeof rule,
+                         cudaMemcpyHostToDevice, ctx->stream));
+  TJM_CU(cudaStreamSynchronize(ctx->stream));
   return TJM_OK;
 }
 

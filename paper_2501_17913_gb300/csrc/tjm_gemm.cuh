@@ -28,45 +28,49 @@ constexpr int kSmemGemm = 32768;
 template <class T> constexpr int gemm_smem_bytes() { return 2 * GB_K * GB_M * (int)sizeof(cx<T>); }
 
 // One layout variant: AK = A's k index is contiguous (else its i index),
-// BJ = B's j index is contiguous (else its k index).  Each thread loads 4
-// elements of A and 4 of B per 16-deep slice; their tile coordinates are fixed
-// per thread, so the loads need no per-element index arithmetic.
-template <class T, bool AK, bool BJ>
+// BJ = B's j index is contiguous (else its k index); TM x TM output tiles
+// (TM = 64 or 32), each thread owning (TM/16) x (TM/16) complex accumulators.
+// Each thread loads TM/16 elements of A and of B per 16-deep slice; their tile
+// coordinates are fixed per thread, so the loads need no per-element index
+// arithmetic.
+template <class T, bool AK, bool BJ, int TM>
 __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* __restrict__ A,
                                        int sai, int sak, int ca, long long sa, const cx<T>* __restrict__ B, int sbk,
                                        int sbj, int cb, long long sb, cx<T>* C, int sci, int scj, long long sc,
                                        bool accumulate, char* smem) {
-  cx<T>* As = reinterpret_cast<cx<T>*>(smem);          // [GB_K][GB_M]
-  cx<T>* Bs = As + GB_K * GB_M;                          // [GB_K][GB_N]
+  constexpr int NQ = TM / 16;              // loads and accumulator rows / columns per thread
+  constexpr int KS = TJM_THREADS / TM;     // k rows covered per load round in the i- / j-contiguous layouts
+  cx<T>* As = reinterpret_cast<cx<T>*>(smem);          // [GB_K][TM]
+  cx<T>* Bs = As + GB_K * TM;                            // [GB_K][TM]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int a_i = AK ? (tid >> 4) : (tid & 63);          // + 16 q   (AK)
-  const int a_k = AK ? (tid & 15) : (tid >> 6);          // + 4 q    (!AK)
-  const int b_j = BJ ? (tid & 63) : (tid >> 4);          // + 16 q   (!BJ)
-  const int b_k = BJ ? (tid >> 6) : (tid & 15);          // + 4 q    (BJ)
-  const int tm = (M + GB_M - 1) / GB_M, tn = (N + GB_N - 1) / GB_N;
+  const int a_i = AK ? (tid >> 4) : (tid % TM);          // + 16 q   (AK)
+  const int a_k = AK ? (tid & 15) : (tid / TM);          // + KS q   (!AK)
+  const int b_j = BJ ? (tid % TM) : (tid >> 4);          // + 16 q   (!BJ)
+  const int b_k = BJ ? (tid / TM) : (tid & 15);          // + KS q   (BJ)
+  const int tm = (M + TM - 1) / TM, tn = (N + TM - 1) / TM;
   const int ntile = batch * tm * tn;
   const int nk = (K + GB_K - 1) / GB_K;
   const T sga = ca ? (T)-1 : (T)1, sgb = cb ? (T)-1 : (T)1;
   for (int t = 0; t < ntile; ++t) {
     const int bt = t / (tm * tn), r0 = t % (tm * tn);
-    const int i0 = (r0 / tn) * GB_M, j0 = (r0 % tn) * GB_N;
+    const int i0 = (r0 / tn) * TM, j0 = (r0 % tn) * TM;
     const cx<T>* Ap = A + bt * sa;
     const cx<T>* Bp = B + bt * sb;
-    cx<T> acc[4][4];
+    cx<T> acc[NQ][NQ];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < NQ; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = czero<T>();
-    cx<T> ra[4], rb[4];
+      for (int c = 0; c < NQ; ++c) acc[r][c] = czero<T>();
+    cx<T> ra[NQ], rb[NQ];
     auto load = [&](int k0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + a_i + (AK ? 16 * q : 0), k = k0 + a_k + (AK ? 0 : 4 * q);
+      for (int q = 0; q < NQ; ++q) {
+        const int i = i0 + a_i + (AK ? 16 * q : 0), k = k0 + a_k + (AK ? 0 : KS * q);
         cx<T> v = czero<T>();
         if (i < M && k < K) v = Ap[i * sai + k * sak];
         v.y *= sga;
         ra[q] = v;
-        const int j = j0 + b_j + (BJ ? 0 : 16 * q), kb = k0 + b_k + (BJ ? 4 * q : 0);
+        const int j = j0 + b_j + (BJ ? 0 : 16 * q), kb = k0 + b_k + (BJ ? KS * q : 0);
         cx<T> u = czero<T>();
         if (j < N && kb < K) u = Bp[kb * sbk + j * sbj];
         u.y *= sgb;
@@ -77,32 +81,32 @@ __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alp
     for (int ks = 0; ks < nk; ++ks) {
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        As[(a_k + (AK ? 0 : 4 * q)) * GB_M + a_i + (AK ? 16 * q : 0)] = ra[q];
-        Bs[(b_k + (BJ ? 4 * q : 0)) * GB_N + b_j + (BJ ? 0 : 16 * q)] = rb[q];
+      for (int q = 0; q < NQ; ++q) {
+        As[(a_k + (AK ? 0 : KS * q)) * TM + a_i + (AK ? 16 * q : 0)] = ra[q];
+        Bs[(b_k + (BJ ? KS * q : 0)) * TM + b_j + (BJ ? 0 : 16 * q)] = rb[q];
       }
       __syncthreads();
       if (ks + 1 < nk) load((ks + 1) * GB_K);
 #pragma unroll 4
       for (int kk = 0; kk < GB_K; ++kk) {
-        cx<T> a[4], bb[4];
+        cx<T> av[NQ], bv[NQ];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = As[kk * GB_M + ty + 16 * r];
+        for (int r = 0; r < NQ; ++r) av[r] = As[kk * TM + ty + 16 * r];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) bb[c] = Bs[kk * GB_N + tx + 16 * c];
+        for (int c = 0; c < NQ; ++c) bv[c] = Bs[kk * TM + tx + 16 * c];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < NQ; ++r)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) cfma(acc[r][c], a[r], bb[c]);
+          for (int c = 0; c < NQ; ++c) cfma(acc[r][c], av[r], bv[c]);
       }
     }
     cx<T>* Cp = C + bt * sc;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < NQ; ++r) {
       const int i = i0 + ty + 16 * r;
       if (i >= M) continue;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < NQ; ++c) {
         const int j = j0 + tx + 16 * c;
         if (j >= N) continue;
         cx<T> v = alpha * acc[r][c];
@@ -115,6 +119,26 @@ __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alp
   __syncthreads();
 }
 
+// Tile choice.  gemm_tile_rule == 0: always 64 x 64 tiles.  == 1: 32 x 32
+// tiles when either output dimension is at most 32 (small bonds, chain ends),
+// where a 64 x 64 tile would leave most of its threads without an output.
+// The rule is a per-launch setting (see the kernel), picked by the host-side
+// autotuner from timed launches.
+__shared__ int gemm_tile_rule;
+
+template <class T, bool AK, bool BJ>
+__device__ __forceinline__ void gemm_layout(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* A, int sai,
+                                            int sak, int ca, long long sa, const cx<T>* B, int sbk, int sbj, int cb,
+                                            long long sb, cx<T>* C, int sci, int scj, long long sc, bool accumulate,
+                                            char* smem) {
+  if (gemm_tile_rule == 1 && (M <= 32 || N <= 32))
+    gemm_core<T, AK, BJ, 32>(batch, M, N, K, alpha, A, sai, sak, ca, sa, B, sbk, sbj, cb, sb, C, sci, scj, sc,
+                             accumulate, smem);
+  else
+    gemm_core<T, AK, BJ, 64>(batch, M, N, K, alpha, A, sai, sak, ca, sa, B, sbk, sbj, cb, sb, C, sci, scj, sc,
+                             accumulate, smem);
+}
+
 // Batched: for b < batch, operands offset by (sa, sb, sc) elements.
 template <class T>
 __device__ __forceinline__ void blk_gemm_batched(int batch, int M, int N, int K, cx<T> alpha, MatA<T> A,
@@ -124,17 +148,17 @@ __device__ __forceinline__ void blk_gemm_batched(int batch, int M, int N, int K,
   const bool ak = A.sk == 1;
   const bool bj = (B.sj == 1) || (B.sk != 1);
   if (ak && bj)
-    gemm_core<T, true, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
-                             B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
-  else if (ak)
-    gemm_core<T, true, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
-                              B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
-  else if (bj)
-    gemm_core<T, false, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk, (int)B.sj,
-                              B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
-  else
-    gemm_core<T, false, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
+    gemm_layout<T, true, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
                                (int)B.sj, B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else if (ak)
+    gemm_layout<T, true, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
+                                (int)B.sj, B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else if (bj)
+    gemm_layout<T, false, true>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
+                                (int)B.sj, B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
+  else
+    gemm_layout<T, false, false>(batch, M, N, K, alpha, A.p, (int)A.si, (int)A.sk, A.conj, sa, B.p, (int)B.sk,
+                                 (int)B.sj, B.conj, sb, C, (int)sci, (int)scj, sc, accumulate, smem);
 }
 
 template <class T>

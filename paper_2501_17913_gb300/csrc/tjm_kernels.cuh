@@ -191,6 +191,8 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   make_ctx(c, S, scr, dims, smem);
   const ProbDev* P = c.P;
   if (S->status != 0) return;
+  if (threadIdx.x == 0) gemm_tile_rule = P->gemm_rule;
+  __syncthreads();
   int step = S->step;
   int flags = S->flags;
   bool ok = true;

@@ -12,6 +12,7 @@ template <class T> struct cx;
 struct ProbDev {
   int L, chi_max, exact, krylov_max;
   int shift_ok;        // MPO in finite-state form: a constant can ride on the on-site channel
+  int gemm_rule;       // GEMM tile rule of this run's slots (0: 64x64 tiles; 1: 32x32 for small outputs)
   int n_jumps, n_obs, n_steps, n_samples;
   double dt, trunc_eps, krylov_tol;
   const int* Dbond;                       // [L + 1] MPO bond dimensions

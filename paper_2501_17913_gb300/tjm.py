@@ -83,6 +83,7 @@ SIGNATURES = [
     ("tjm_run_set_state", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.POINTER(C.c_int),
                                     C.POINTER(C.c_double)]),
     ("tjm_run_status", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int)]),
+    ("tjm_run_set_tile_rule", C.c_int, [C.c_void_p, C.c_int64, C.c_int]),
     ("tjm_run_free", C.c_int, [C.c_void_p, C.c_int64]),
     ("tjm_stream", C.c_void_p, [C.c_void_p]),
     ("tjm_sync", C.c_int, [C.c_void_p]),
@@ -171,6 +172,8 @@ class Context:
             raise TJMError(st, "tjm_create failed")
         self.h = h
         self.L = L
+        self.precision = precision
+        self.chi_max = int(chi_max)
         self.runs = {}
 
     def _check(self, st, what):
@@ -279,6 +282,10 @@ class Context:
         st = np.zeros(n_traj, dtype=np.int32)
         self._check(self.lib.tjm_run_status(self.h, run_id, st.ctypes.data_as(C.POINTER(C.c_int))), "tjm_run_status")
         return st
+
+    def set_tile_rule(self, run_id, rule):
+        """GEMM tile rule for the run's later launches (0: 64x64 tiles, 1: 32x32 for small outputs)."""
+        self._check(self.lib.tjm_run_set_tile_rule(self.h, run_id, int(rule)), "tjm_run_set_tile_rule")
 
     def free(self, run_id):
         self._check(self.lib.tjm_run_free(self.h, run_id), "tjm_run_free")
