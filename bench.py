@@ -210,8 +210,13 @@ def main():
     rid = ctx.prepare(psi, N, 0, obs, times, first_traj=rank * N)
     stream = torch.cuda.ExternalStream(ctx.stream())
     ctx.advance(rid, 0)                      # initialisation, F_0
+    # warm-up steps double as the GEMM tile autotuner's trial launches
+    from paper_2501_17913_gb300.autotune import TileAutotuner
+    tuner = TileAutotuner()
     for _ in range(a.warmup):
-        ctx.advance(rid, 1)
+        tuner.advance(ctx, rid, 1)
+    rule = tuner.next_rule(tuner.key(ctx))
+    ctx.set_tile_rule(rid, rule)
     ctx.sync()
     s0 = ctx.stats(rid)
     launches0 = ctx.launches()
@@ -267,7 +272,7 @@ def main():
     if not a.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx2 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local)
+        ctx2 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local, tile_rule=rule)
         times2 = [dt * j for j in range(a.steps + 1)]
         r2 = ctx2.run(psi, N, 0, obs, times2, first_traj=rank * N)
         mean, sem, pt = ctx2.result(r2)
@@ -316,6 +321,7 @@ def main():
                           (N * (L * 2 * chi * chi + 2 * (L + 1) * 5 * chi * chi) * (8 if prec else 16) / 1e9),
                           "parallelism": "trajectories" + ("x%d" % world if world > 1 else "")},
                "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
+               "tile_autotune": {"rule": rule, "trials": tuner.report()},
                "e2e": e2e, "cpu_baseline": cpu,
                "stats": {"jumps": s1["jumps"] - s0["jumps"],
                          "matvecs_one_site": s1["matvec_one_site"] - s0["matvec_one_site"],

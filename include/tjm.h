@@ -100,6 +100,7 @@ typedef struct {
                          * and last MPO channels).  A constant shift only changes the global phase,
                          * so observables are unchanged; it keeps the FP32 environment sums near
                          * zero instead of near the extensive energy.  0: evolve with H as given. */
+  int tile_rule;        /* initial GEMM tile rule of new runs (see tjm_run_set_tile_rule); default 0 */
 } tjm_options;
 
 /* Fill opts with the defaults above. */

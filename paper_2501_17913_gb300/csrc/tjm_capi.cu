@@ -262,6 +262,7 @@ void tjm_default_options(tjm_options* o) {
   o->device = 0;
   o->max_ctas = 0;
   o->energy_shift = 1;
+  o->tile_rule = 0;
 }
 
 const char* tjm_last_error(const tjm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -278,6 +279,7 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   if (opts) ctx->opt = *opts;
   tjm_options& o = ctx->opt;
   if (o.precision < 0 || o.precision > 2) return fail(nullptr, TJM_EINVAL, "");
+  if (o.tile_rule < 0 || o.tile_rule > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.krylov_max <= 0 || o.krylov_max > 30) o.krylov_max = 30;
   if (!(o.krylov_tol > 0)) o.krylov_tol = o.precision == TJM_PREC_FP64 ? 1e-12 : 1e-7;
   const int L = H->L;
@@ -551,7 +553,7 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   // problem descriptor of this run
   tjm::ProbDev P;
   std::memset(&P, 0, sizeof P);
-  P.L = L; P.shift_ok = ctx->shift_ok; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
+  P.L = L; P.shift_ok = ctx->shift_ok; P.gemm_rule = ctx->opt.tile_rule; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
   P.n_jumps = ctx->n_jumps; P.n_obs = n_obs; P.n_steps = R.n_steps; P.n_samples = n_times;
   P.dt = dt; P.trunc_eps = ctx->trunc_eps; P.krylov_tol = ctx->opt.krylov_tol;
   P.Dbond = ctx->d_Dbond;

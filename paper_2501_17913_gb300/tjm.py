@@ -40,7 +40,7 @@ class tjm_state(C.Structure):
 class tjm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int),
-                ("energy_shift", C.c_int)]
+                ("energy_shift", C.c_int), ("tile_rule", C.c_int)]
 
 
 class tjm_stats(C.Structure):
@@ -147,7 +147,7 @@ class Context:
     """One TJM problem (tjm_create) and the runs started on it."""
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32, krylov_max=30, krylov_tol=0.0,
-                 exact=False, device=0, max_ctas=0, energy_shift=True):
+                 exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0):
         lib = load()
         self.lib = lib
         L = len(W)
@@ -165,6 +165,7 @@ class Context:
         opt.precision, opt.krylov_max, opt.krylov_tol = precision, krylov_max, krylov_tol
         opt.exact_full_bond, opt.device, opt.max_ctas = int(bool(exact)), device, max_ctas
         opt.energy_shift = int(bool(energy_shift))
+        opt.tile_rule = int(tile_rule)
         h = C.c_void_p()
         st = lib.tjm_create(C.byref(h), C.byref(mpo), js, len(jumps), float(dt), int(chi_max), float(trunc_eps),
                             C.byref(opt))
