@@ -54,8 +54,11 @@ class Request:
 
 class Server:
     def __init__(self, precision=tjm.PREC_FP32_DEC32, mem_budget=None, steps_per_tick=1, device=0,
-                 keep_per_traj=False):
+                 keep_per_traj=False, tuner=None):
         tjm.load()
+        # GEMM tile rules tuned by earlier stepped runs of this process (autotune.TileAutotuner);
+        # a request whose (precision, chi_max) has no tuned rule runs with the default
+        self.tuner = tuner
         self.precision = precision
         self.steps = steps_per_tick
         self.device = device
@@ -94,8 +97,9 @@ class Server:
                 still.append(r)          # wait for memory; admit in arrival order
                 continue
             wl = r.wl
+            rule = self.tuner.best.get((int(self.precision), int(wl.chi_max)), 0) if self.tuner else 0
             r.ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=self.precision,
-                                device=self.device)
+                                device=self.device, tile_rule=rule)
             psi = np.array(wl.psi0_per_traj) if wl.psi0_per_traj is not None else np.array(wl.psi0)
             r.run = r.ctx.prepare(psi, wl.n_traj, wl.seed, wl.observables, wl.times,
                                   first_traj=wl.meta.get('first_traj', 0))
