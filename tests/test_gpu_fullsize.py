@@ -28,6 +28,7 @@ GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 # (last step checked, tolerance) per precision on the L=30 chain
 HORIZON = {tjm.PREC_FP64: (30, 1e-10), tjm.PREC_FP32: (20, 1e-4), tjm.PREC_FP32_DEC32: (5, 1e-4)}
 FP64_ALL_STEPS = 1e-6
+_CACHE = {}     # the FP64 L=30 ensemble, shared by the FP32-path comparisons
 
 
 def _gold(name):
@@ -96,9 +97,12 @@ def test_l30_1024_trajectories_ensemble_fp32_vs_fp64(prec):
     _check_properties(pt, st, wl.chi_max)
     last, tol = HORIZON[prec]
     _compare_sampled(pt, g, tol, 1e-4, last_step=last)
-    pt64, mean64, sem64, st64, _, ctx = run_gpu(wl, tjm.PREC_FP64)
-    ctx.close()
-    _check_properties(pt64, st64, wl.chi_max)
+    if "l30_fp64" not in _CACHE:
+        pt64, mean64, sem64, st64, _, ctx = run_gpu(wl, tjm.PREC_FP64)
+        ctx.close()
+        _check_properties(pt64, st64, wl.chi_max)
+        _CACHE["l30_fp64"] = (mean64, sem64)
+    mean64, sem64 = _CACHE["l30_fp64"]
     se = np.sqrt(sem ** 2 + sem64 ** 2)
     se = np.maximum(se, 1e-4)
     z = np.abs(mean - mean64) / se
