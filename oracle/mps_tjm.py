@@ -98,8 +98,8 @@ def rq_move_left(mps, l):
 def trunc_rank(S, prob: Problem, rec=None) -> int:
     """Number of singular values kept after a two-site update or a jump.
 
-    Reading of the paper's "some threshold" (Sec. 1TDVP and 2TDVP as tensor
-    networks): keep the smallest r >= 1 with sum_{i>=r} S_i^2 <= trunc_eps *
+    Reading of the unspecified cut-off of Sec. 1TDVP and 2TDVP as tensor
+    networks: keep the smallest r >= 1 with sum_{i>=r} S_i^2 <= trunc_eps *
     sum_i S_i^2 (relative discarded weight), capped at chi_max.  In exact mode
     every singular value is kept, zeros included.
     """
