@@ -237,6 +237,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       const cx<Tc>* vkm = c.krylov + (long long)(k > 0 ? k - 1 : 0) * n;
       const Tc bm = k > 0 ? (Tc)beta[k - 1] : (Tc)0;
       Tc ax = 0;
+      #pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
         cx<Tc> t = c.w[i];
         if (k > 0) { t.x -= bm * vkm[i].x; t.y -= bm * vkm[i].y; }
@@ -256,6 +257,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
         cx<Tc> acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = czero<Tc>();
+        #pragma unroll 2
         for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
           cx<Tc> wi = c.w[i];
           if (j0 == 0) {   // each thread updates, then rereads, only its own entries
@@ -289,8 +291,10 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       for (int j = threadIdx.x; j < nb; j += TJM_THREADS) hw[j] = mk((Tc)hh[2 * j], (Tc)hh[2 * j + 1]);
       __syncthreads();
       Tc n2 = 0;
+      #pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
         cx<Tc> t = c.w[i];
+#pragma unroll 4
         for (int j = 0; j < nb; ++j) t = t - hw[j] * c.krylov[(long long)j * n + i];
         c.w[i] = t;
         n2 = fma(t.x, t.x, n2);
@@ -319,6 +323,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
   cx<Tc>* cw = reinterpret_cast<cx<Tc>*>(c.red);
   for (int j = threadIdx.x; j < nk; j += TJM_THREADS) cw[j] = mk((Tc)(b0 * cf[j].x), (Tc)(b0 * cf[j].y));
   __syncthreads();
+  #pragma unroll 2
   for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
     cx<Tc> acc = czero<Tc>();
     for (int j = 0; j < nk; ++j) cfma(acc, cw[j], c.krylov[(long long)j * n + i]);
