@@ -231,17 +231,21 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
     // chunks of 8 basis vectors; (3) w -= sum_j h_j v_j while forming ||w||^2.
     // Coefficients are reduced in FP64; alpha_k = alpha + Re h_k.
     const int nb = k + 1;
-    const cx<Tc>* vk0 = c.krylov + (long long)k * n;
+    // w and the basis are distinct buffers: say so, so loads of later
+    // elements may be issued ahead of the stores to w
+    cx<Tc>* __restrict__ wv = c.w;
+    const cx<Tc>* __restrict__ kb = c.krylov;
+    const cx<Tc>* __restrict__ vk0 = kb + (long long)k * n;
     double al_k;
     {
-      const cx<Tc>* vkm = c.krylov + (long long)(k > 0 ? k - 1 : 0) * n;
+      const cx<Tc>* __restrict__ vkm = kb + (long long)(k > 0 ? k - 1 : 0) * n;
       const Tc bm = k > 0 ? (Tc)beta[k - 1] : (Tc)0;
       Tc ax = 0;
       #pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-        cx<Tc> t = c.w[i];
+        cx<Tc> t = wv[i];
         if (k > 0) { t.x -= bm * vkm[i].x; t.y -= bm * vkm[i].y; }
-        c.w[i] = t;
+        wv[i] = t;
         const cx<Tc> v = vk0[i];
         ax = fma(v.x, t.x, fma(v.y, t.y, ax));
       }
@@ -259,16 +263,16 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
         for (int q = 0; q < 8; ++q) acc[q] = czero<Tc>();
         #pragma unroll 2
         for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-          cx<Tc> wi = c.w[i];
+          cx<Tc> wi = wv[i];
           if (j0 == 0) {   // each thread updates, then rereads, only its own entries
             const cx<Tc> v = vk0[i];
             wi.x -= a0 * v.x;
             wi.y -= a0 * v.y;
-            c.w[i] = wi;
+            wv[i] = wi;
           }
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            if (q < jn) cfma_cj(acc[q], c.krylov[(long long)(j0 + q) * n + i], wi);
+            if (q < jn) cfma_cj(acc[q], kb[(long long)(j0 + q) * n + i], wi);
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -293,10 +297,10 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       Tc n2 = 0;
       #pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
-        cx<Tc> t = c.w[i];
+        cx<Tc> t = wv[i];
 #pragma unroll 4
-        for (int j = 0; j < nb; ++j) t = t - hw[j] * c.krylov[(long long)j * n + i];
-        c.w[i] = t;
+        for (int j = 0; j < nb; ++j) t = t - hw[j] * kb[(long long)j * n + i];
+        wv[i] = t;
         n2 = fma(t.x, t.x, n2);
         n2 = fma(t.y, t.y, n2);
       }

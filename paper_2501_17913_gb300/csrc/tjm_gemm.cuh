@@ -178,8 +178,8 @@ __device__ __forceinline__ void blk_gemm(int M, int N, int K, MatA<T> A, MatB<T>
 // (so0 + t * so_step, si0 + t * si_step), t < nsh: this is how a constant
 // times the identity rides on an MPO's on-site channel.
 template <class T>
-__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* in,
-                                        long long sip, long long sii, cx<T>* out, long long sop, long long soo,
+__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* __restrict__ in,
+                                        long long sip, long long sii, cx<T>* __restrict__ out, long long sop, long long soo,
                                         char* smem, double shift = 0.0, int nsh = 0, int so0 = 0, int so_step = 1,
                                         int si0 = 0, int si_step = 1) {
   cx<T>* val = reinterpret_cast<cx<T>*>(smem);                      // [O * I]
