@@ -27,17 +27,25 @@ constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 constexpr int kSmemGemm = 32768;
 template <class T> constexpr int gemm_smem_bytes() { return 2 * GB_K * GB_M * (int)sizeof(cx<T>); }
 
+// A operand formed on the fly from an MPO block in row-sparse form (see
+// blk_wgemm): A(i, k) = sum_z val[z] t1[x * sip + col[z] * chr + b] over the
+// entries z of MPO row o = t * Dr + v, with i = x * dd + t and k = v * chr + b.
+template <class T> struct WaArgs {
+  const cx<T>* val; const int* col; const int* rp;
+  const cx<T>* t1; int sip, dd, Dr, chr;
+};
+
 // One layout variant: AK = A's k index is contiguous (else its i index),
 // BJ = B's j index is contiguous (else its k index); TM x TM output tiles
 // (TM = 64 or 32), each thread owning (TM/16) x (TM/16) complex accumulators.
 // Each thread loads TM/16 elements of A and of B per 16-deep slice; their tile
 // coordinates are fixed per thread, so the loads need no per-element index
 // arithmetic.
-template <class T, bool AK, bool BJ, int TM>
+template <class T, bool AK, bool BJ, int TM, bool WA = false>
 __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* __restrict__ A,
                                        int sai, int sak, int ca, long long sa, const cx<T>* __restrict__ B, int sbk,
                                        int sbj, int cb, long long sb, cx<T>* C, int sci, int scj, long long sc,
-                                       bool accumulate, char* smem) {
+                                       bool accumulate, char* smem, WaArgs<T> wa = WaArgs<T>{}) {
   constexpr int NQ = TM / 16;              // loads and accumulator rows / columns per thread
   constexpr int KS = TJM_THREADS / TM;     // k rows covered per load round in the i- / j-contiguous layouts
   cx<T>* As = reinterpret_cast<cx<T>*>(smem);          // [GB_K][TM]
@@ -67,8 +75,19 @@ __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alp
       for (int q = 0; q < NQ; ++q) {
         const int i = i0 + a_i + (AK ? 16 * q : 0), k = k0 + a_k + (AK ? 0 : KS * q);
         cx<T> v = czero<T>();
-        if (i < M && k < K) v = Ap[i * sai + k * sak];
-        v.y *= sga;
+        if constexpr (WA) {
+          if (i < M && k < K) {
+            const int x = i / wa.dd, t = i - x * wa.dd;
+            const int vv = k / wa.chr, b = k - vv * wa.chr;
+            const int o = t * wa.Dr + vv;
+            const cx<T>* src = wa.t1 + (long long)x * wa.sip + b;
+            const int z1 = wa.rp[o + 1];
+            for (int z = wa.rp[o]; z < z1; ++z) cfma(v, wa.val[z], src[wa.col[z] * wa.chr]);
+          }
+        } else {
+          if (i < M && k < K) v = Ap[i * sai + k * sak];
+          v.y *= sga;
+        }
         ra[q] = v;
         const int j = j0 + b_j + (BJ ? 0 : 16 * q), kb = k0 + b_k + (BJ ? KS * q : 0);
         cx<T> u = czero<T>();
@@ -177,14 +196,14 @@ __device__ __forceinline__ void blk_gemm(int M, int N, int K, MatA<T> A, MatB<T>
 // A scalar `shift` can be added on nsh diagonal entries (o, i) =
 // (so0 + t * so_step, si0 + t * si_step), t < nsh: this is how a constant
 // times the identity rides on an MPO's on-site channel.
+// Row-sparse form of Wm (+ the shift entries) in shared memory at csr:
+// val [O * I], col [O * I], rp [O + 1].  Ends with a barrier.
 template <class T>
-__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* __restrict__ in,
-                                        long long sip, long long sii, cx<T>* __restrict__ out, long long sop, long long soo,
-                                        char* smem, double shift = 0.0, int nsh = 0, int so0 = 0, int so_step = 1,
-                                        int si0 = 0, int si_step = 1) {
-  cx<T>* val = reinterpret_cast<cx<T>*>(smem);                      // [O * I]
-  int* col = reinterpret_cast<int*>(val + O * I);                    // [O * I]
-  int* rp = col + O * I;                                             // [O + 1]
+__device__ __forceinline__ void wcsr_build(int O, int I, const cx<double>* Wm, char* csr, double shift, int nsh,
+                                           int so0, int so_step, int si0, int si_step) {
+  cx<T>* val = reinterpret_cast<cx<T>*>(csr);
+  int* col = reinterpret_cast<int*>(val + O * I);
+  int* rp = col + O * I;
   __syncthreads();
   if (threadIdx.x < 32) {
     const int o = threadIdx.x;
@@ -216,6 +235,17 @@ __device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<dou
     }
   }
   __syncthreads();
+}
+
+template <class T>
+__device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<double>* Wm, const cx<T>* __restrict__ in,
+                                        long long sip, long long sii, cx<T>* __restrict__ out, long long sop, long long soo,
+                                        char* smem, double shift = 0.0, int nsh = 0, int so0 = 0, int so_step = 1,
+                                        int si0 = 0, int si_step = 1) {
+  const cx<T>* val = reinterpret_cast<const cx<T>*>(smem);
+  const int* col = reinterpret_cast<const int*>(val + O * I);
+  const int* rp = col + O * I;
+  wcsr_build<T>(O, I, Wm, smem, shift, nsh, so0, so_step, si0, si_step);
   const long long tot = (long long)P * Q;
   for (long long e = threadIdx.x; e < tot; e += TJM_THREADS) {
     const int p = (int)(e / Q), q = (int)(e % Q);
@@ -229,6 +259,35 @@ __device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<dou
     }
   }
   __syncthreads();
+}
+
+// y[(x t)][j] = sum_(v b) [sum_(w s) Wm[(t v)][(w s)] t1[x][(w s)][b]] R[(v b)][j]
+// for x < P, t < dd, j < chr: the MPO contraction and the second GEMM of an
+// effective-Hamiltonian application in one pass.  The MPO block is applied
+// while G3's A tile is loaded, so the (P dd) x (Dr chr) intermediate is never
+// written.  FP32 only: the row-sparse MPO sits in shared memory above the
+// GEMM staging tiles (16 KB of the 32 KB GEMM area).
+template <class T>
+__device__ __noinline__ void blk_wgemm(int P, int dd, int Dr, int I, int chr, const cx<double>* Wm,
+                                       const cx<T>* __restrict__ t1, const cx<T>* R, cx<T>* y, char* smem,
+                                       double shift, int nsh, int so0, int so_step, int si0, int si_step) {
+  static_assert(sizeof(T) == 4, "fused MPO GEMM is for FP32 contractions");
+  const int O = dd * Dr;
+  char* csr = smem + 2 * GB_K * 64 * (int)sizeof(cx<T>);
+  wcsr_build<T>(O, I, Wm, csr, shift, nsh, so0, so_step, si0, si_step);
+  WaArgs<T> wa;
+  wa.val = reinterpret_cast<const cx<T>*>(csr);
+  wa.col = reinterpret_cast<const int*>(wa.val + O * I);
+  wa.rp = wa.col + O * I;
+  wa.t1 = t1; wa.sip = I * chr; wa.dd = dd; wa.Dr = Dr; wa.chr = chr;
+  const int M = P * dd, N = chr, K = Dr * chr;
+  const cx<T> one = mk((T)1, (T)0);
+  if (gemm_tile_rule == 1 && (M <= 32 || N <= 32))
+    gemm_core<T, true, true, 32, true>(1, M, N, K, one, nullptr, 0, 1, 0, 0, R, chr, 1, 0, 0, y, chr, 1, 0, false,
+                                       smem, wa);
+  else
+    gemm_core<T, true, true, 64, true>(1, M, N, K, one, nullptr, 0, 1, 0, 0, R, chr, 1, 0, 0, y, chr, 1, 0, false,
+                                       smem, wa);
 }
 
 }  // namespace tjm
