@@ -25,8 +25,10 @@ from gpu_common import lib_ready, run_gpu
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
-# (last step checked, tolerance) per precision on the L=30 chain
-HORIZON = {tjm.PREC_FP64: (30, 1e-10), tjm.PREC_FP32: (20, 1e-4), tjm.PREC_FP32_DEC32: (5, 1e-4)}
+# (last step checked, tolerance, decision margin) per precision on the L=30 chain: a decision can
+# flip only when its margin is below the difference in the state, so the FP64 margin is tiny
+HORIZON = {tjm.PREC_FP64: (25, 1e-10, 1e-8), tjm.PREC_FP32: (20, 1e-4, 1e-4),
+           tjm.PREC_FP32_DEC32: (5, 1e-4, 1e-4)}
 FP64_ALL_STEPS = 1e-6
 _CACHE = {}     # the FP64 L=30 ensemble, shared by the FP32-path comparisons
 
@@ -80,25 +82,27 @@ def test_l30_sampled_trajectories_to_horizon(prec):
     g = _gold("l30")
     wl = I.config_l30()
     pt = _sampled_runs(wl, g, prec)
-    last, tol = HORIZON[prec]
-    _compare_sampled(pt, g, tol, 1e-4, last_step=last)
+    last, tol, margin = HORIZON[prec]
+    _compare_sampled(pt, g, tol, margin, last_step=last)
     if prec == tjm.PREC_FP64:
-        _compare_sampled(pt, g, FP64_ALL_STEPS, 1e-4)
+        _compare_sampled(pt, g, FP64_ALL_STEPS, margin)
 
 
 @pytest.mark.parametrize("prec", [tjm.PREC_FP32_DEC32])
 def test_l30_1024_trajectories_ensemble_fp32_vs_fp64(prec):
     """All 1024 L=30 trajectories for 100 steps: properties of every trajectory, the sampled ones to the
-    horizon, and the FP32 ensemble mean within 3 standard errors of the FP64 ensemble mean."""
+    horizon, and the FP32 ensemble mean within 3 standard errors of an FP64 ensemble (the first 256
+    trajectory ids: FP64 factorizations run at GB300's FP64 rate, so 1024 of them would take
+    minutes; the combined standard error accounts for the smaller sample)."""
     g = _gold("l30")
     wl = I.config_l30()
     pt, mean, sem, st, _, ctx = run_gpu(wl, prec)
     ctx.close()
     _check_properties(pt, st, wl.chi_max)
-    last, tol = HORIZON[prec]
-    _compare_sampled(pt, g, tol, 1e-4, last_step=last)
+    last, tol, margin = HORIZON[prec]
+    _compare_sampled(pt, g, tol, margin, last_step=last)
     if "l30_fp64" not in _CACHE:
-        pt64, mean64, sem64, st64, _, ctx = run_gpu(wl, tjm.PREC_FP64)
+        pt64, mean64, sem64, st64, _, ctx = run_gpu(wl, tjm.PREC_FP64, n_traj=256)
         ctx.close()
         _check_properties(pt64, st64, wl.chi_max)
         _CACHE["l30_fp64"] = (mean64, sem64)
