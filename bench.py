@@ -149,27 +149,44 @@ def oracle_sample(cores, L=24, chi=64, rounds=1):
             "wall_s": wall, "cpu_s": busy}
 
 
+def workload_config(a, world, state_bytes_per_elem):
+    L, chi, N = a.L, a.chi, a.ntraj
+    return {"workload": "xxx_L%d_chi%d_N%d_random_chi_saturated" % (L, chi, N), "L": L, "chi_max": chi,
+            "trajectories_per_gpu": N, "dt": 0.1, "gamma": 0.1, "g": 0.5,
+            "precision": a.precision, "l2": "inputs larger than L2 (trajectory state %.1f GB)" %
+            (N * (L * 2 * chi * chi + 2 * (L + 1) * 5 * chi * chi) * state_bytes_per_elem / 1e9),
+            "parallelism": "trajectories" + ("x%d" % world if world > 1 else "")}
+
+
 def run_reference(a):
+    """The oracle arm: the CPU FP64 oracle on the bench workload, one trajectory per host core.
+
+    Each timed step is one oracle TJM step of `cores` trajectories of the L-site random chi-saturated
+    MPS (the bench's seed), in parallel; the warm-up steps run the same code on a 24-site chain.
+    """
     cores = max(1, min(os.cpu_count() or 1, 16))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(a.warmup):
-        oracle_sample(cores, rounds=1)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import multiprocessing as mp
     t0 = time.perf_counter()
-    tot = 0.0
-    for _ in range(a.steps):
-        r = oracle_sample(cores, rounds=1)
-        tot += r["cpu_s"] / cores
-    value = a.steps * cores * 24 / tot
-    ms = 1000.0 * tot / a.steps
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(a.warmup):
+            pool.map(_oracle_step_job, [(24, a.chi, t, 11) for t in range(cores)])
+        busy = 0.0
+        for k in range(a.steps):
+            per = pool.map(_oracle_step_job, [(a.L, a.chi, k * cores + t, 2025) for t in range(cores)])
+            busy += sum(per) / cores
+    value = a.steps * cores * a.L / busy
+    ms = 1000.0 * busy / a.steps
+    sample = ("%d trajectories (one per core) x 1 oracle TJM step per timed step, of the L=%d chi=%d random "
+              "chi-saturated MPS (seed 2025), numpy FP64" % (cores, a.L, a.chi))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference",
-           "config": {"workload": "xxx_L24_chi64_oracle_sample", "note": "CPU FP64 oracle; per-site rate of "
-                      "one TJM step on a chi=64-saturated chain, one trajectory per core"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "%d trajectories x 1 step per timed step, L=24, chi=64" % cores},
+           "data": "synthetic", "impl": "reference", "config": workload_config(a, 1, 16),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": time.perf_counter() - t0}
     print(json.dumps(out), flush=True)
@@ -315,11 +332,7 @@ def main():
                "vs_baseline": None,
                "dtype": {"fp32": "f32", "fp32d64": "f32+f64", "fp64": "f64"}[a.precision],
                "data": "synthetic",
-               "config": {"workload": "xxx_L%d_chi%d_N%d_random_chi_saturated" % (L, chi, N), "L": L, "chi_max": chi,
-                          "trajectories_per_gpu": N, "dt": dt, "gamma": 0.1, "g": 0.5,
-                          "precision": a.precision, "l2": "inputs larger than L2 (trajectory state %.1f GB)" %
-                          (N * (L * 2 * chi * chi + 2 * (L + 1) * 5 * chi * chi) * (8 if prec else 16) / 1e9),
-                          "parallelism": "trajectories" + ("x%d" % world if world > 1 else "")},
+               "config": workload_config(a, world, 8 if prec else 16),
                "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
                "tile_autotune": {"rule": rule, "trials": tuner.report()},
                "e2e": e2e, "cpu_baseline": cpu,
