@@ -7,7 +7,9 @@
 //   * exp(i theta T) e_1 for the Lanczos tridiagonal T by a scaled Taylor
 //     series on one warp (Moler & Van Loan, "Nineteen dubious ways...", the
 //     series method with scaling), with a Gershgorin-centred shift.
-// Matrices live in global (L2-resident) per-CTA workspace, column-major.
+// Matrices are column-major, in the CTA's shared-memory workspace when the
+// factorization precision is FP32 and they fit (64 KB), else in its global
+// scratch.  Column (pair) work is dealt to aligned groups of 8 lanes.
 #pragma once
 #include "tjm_common.cuh"
 
