@@ -151,6 +151,13 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
 /* tjm_poll -- TJM_OK if the run's device work has finished, TJM_EBUSY if not. */
 tjm_status tjm_poll(tjm_ctx* ctx, int64_t run_id);
 
+/* tjm_wait -- bounded host wait for the run's device work (its last launch):
+ * TJM_OK once finished, TJM_ETIMEOUT if it is still executing after timeout_s
+ * seconds (the work continues; wait or poll again later).  No device code
+ * waits on anything, so this host wait is the only wait that needs a bound.
+ * TJM_EINVAL for a negative timeout or an unknown run. */
+tjm_status tjm_wait(tjm_ctx* ctx, int64_t run_id, double timeout_s);
+
 /* tjm_result -- wait for the run and copy results.
  *   mean, sem  [n_times][n_obs]: trajectory average and standard error of the
  *              mean (Eq. TJMExpVal), may be NULL.

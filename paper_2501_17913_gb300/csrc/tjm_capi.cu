@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -13,6 +14,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tjm.h"
@@ -738,6 +740,21 @@ tjm_status tjm_poll(tjm_ctx* ctx, int64_t run_id) {
   if (e == cudaErrorNotReady) return TJM_EBUSY;
   if (e != cudaSuccess) return fail(ctx, TJM_ECUDA, "poll: %s", cudaGetErrorString(e));
   return TJM_OK;
+}
+
+tjm_status tjm_wait(tjm_ctx* ctx, int64_t run_id, double timeout_s) {
+  if (!ctx || !(timeout_s >= 0.0)) return TJM_EINVAL;
+  Run* R = find_run(ctx, run_id);
+  if (!R) return fail(ctx, TJM_EINVAL, "unknown run");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(R->done);
+    if (e == cudaSuccess) return TJM_OK;
+    if (e != cudaErrorNotReady) return fail(ctx, TJM_ECUDA, "wait: %s", cudaGetErrorString(e));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= timeout_s) return fail(ctx, TJM_ETIMEOUT, "run %lld still executing after %.3f s", (long long)run_id, el);
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
 }
 
 tjm_status tjm_sync(tjm_ctx* ctx) {

@@ -84,6 +84,7 @@ SIGNATURES = [
                                     C.POINTER(C.c_double)]),
     ("tjm_run_status", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int)]),
     ("tjm_run_set_tile_rule", C.c_int, [C.c_void_p, C.c_int64, C.c_int]),
+    ("tjm_wait", C.c_int, [C.c_void_p, C.c_int64, C.c_double]),
     ("tjm_run_free", C.c_int, [C.c_void_p, C.c_int64]),
     ("tjm_stream", C.c_void_p, [C.c_void_p]),
     ("tjm_sync", C.c_int, [C.c_void_p]),
@@ -221,6 +222,14 @@ class Context:
 
     def advance(self, run_id, max_steps):
         self._check(self.lib.tjm_run_advance(self.h, run_id, int(max_steps)), "tjm_run_advance")
+
+    def wait(self, run_id, timeout_s):
+        """True once the run's device work has finished, False if it is still running after timeout_s."""
+        st = self.lib.tjm_wait(self.h, run_id, float(timeout_s))
+        if st == TJM_ETIMEOUT:
+            return False
+        self._check(st, "tjm_wait")
+        return True
 
     def poll(self, run_id):
         st = self.lib.tjm_poll(self.h, run_id)
