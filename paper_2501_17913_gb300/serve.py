@@ -54,8 +54,12 @@ class Request:
 
 class Server:
     def __init__(self, precision=tjm.PREC_FP32_DEC32, mem_budget=None, steps_per_tick=1, device=0,
-                 keep_per_traj=False, tuner=None):
-        tjm.load()
+                 keep_per_traj=False, tuner=None, backend=tjm, clock=time.perf_counter):
+        # backend: the library binding (tjm); a stand-in with the same names lets the host logic
+        # run without a GPU
+        self.tj = backend
+        self.clock = clock
+        self.tj.load()
         # GEMM tile rules tuned by earlier stepped runs of this process (autotune.TileAutotuner);
         # a request whose (precision, chi_max) has no tuned rule runs with the default
         self.tuner = tuner
@@ -76,11 +80,11 @@ class Server:
         self.launches = 0
         # anchor context: owns the launch stream and the per-CTA scratch of every batched launch
         W = I.xxx_mpo(2, 0.0, 0.0)
-        self.anchor = tjm.Context(W, [], 0.1, 1, 0.0, precision=precision, device=device)
+        self.anchor = self.tj.Context(W, [], 0.1, 1, 0.0, precision=precision, device=device)
         self.anchor_run = self.anchor.prepare(None, 1, 0, [], [0.0])
 
     def submit(self, wl, arrival=None):
-        r = Request(self.next_id, wl, time.perf_counter() if arrival is None else arrival)
+        r = Request(self.next_id, wl, self.clock() if arrival is None else arrival)
         r.bytes = state_bytes(wl, self.precision)
         r.work = float(wl.n_traj) * wl.L * wl.n_steps
         self.next_id += 1
@@ -98,8 +102,8 @@ class Server:
                 continue
             wl = r.wl
             rule = self.tuner.best.get((int(self.precision), int(wl.chi_max)), 0) if self.tuner else 0
-            r.ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=self.precision,
-                                device=self.device, tile_rule=rule)
+            r.ctx = self.tj.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=self.precision,
+                                    device=self.device, tile_rule=rule)
             psi = np.array(wl.psi0_per_traj) if wl.psi0_per_traj is not None else np.array(wl.psi0)
             r.run = r.ctx.prepare(psi, wl.n_traj, wl.seed, wl.observables, wl.times,
                                   first_traj=wl.meta.get('first_traj', 0))
@@ -110,12 +114,12 @@ class Server:
 
     def tick(self):
         """Admit, run one batched launch, retire.  Returns False when idle with nothing queued."""
-        now = time.perf_counter()
+        now = self.clock()
         self._admit(now)
         if not self.active:
             return bool(self.queue)
         pairs = [(self.anchor, self.anchor_run)] + [(r.ctx, r.run) for r in self.active]
-        tjm.group_advance(pairs, self.steps)
+        self.tj.group_advance(pairs, self.steps)
         self.launches += 1
         self.anchor.sync()
         still = []
@@ -125,7 +129,7 @@ class Server:
                 r.mean, r.sem, pt = r.ctx.result(r.run, per_traj=self.keep, allow_numeric=True)
                 if self.keep:
                     r.per_traj = pt
-                r.done = time.perf_counter()
+                r.done = self.clock()
                 r.ctx.free(r.run)
                 r.ctx.close()
                 self.used -= r.bytes
@@ -138,7 +142,7 @@ class Server:
     def drain(self):
         while self.tick():
             if not self.active and self.queue:
-                time.sleep(max(0.0, min(q.arrival for q in self.queue) - time.perf_counter()))
+                time.sleep(max(0.0, min(q.arrival for q in self.queue) - self.clock()))
         return self.finished
 
     def report(self, t0, t1):
