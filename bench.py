@@ -253,7 +253,7 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     s1 = ctx.stats(rid)
-    gpu_launches = (ctx.launches() - launches0) * 2   # each advance: one counter memset + one trajectory kernel
+    gpu_launches = ctx.launches() - launches0   # trajectory-kernel launches (each preceded by a counter memset)
     t_max = ms
     if dist:
         t = torch.tensor([ms], device="cuda")
