@@ -418,3 +418,34 @@ def test_lindblad_pure_relaxation_closed_form():
         for l in range(L):
             assert abs(O2.expect(r, I.Z, l, L) - (1 - 2 * p1[l] * math.exp(-g * t))) < 1e-10
     assert abs(rhos[-1][0, 0].real - 1.0) < 1e-8
+
+
+# ---------------------------------------------------------------- energy shift (a global phase)
+def _shifted_mpo(W, c):
+    """The MPO with -c*I added to every site's on-site entry (row 0, last column): H - c*L*I."""
+    out = []
+    for l, w in enumerate(W):
+        w = np.array(w, dtype=np.complex128)
+        w[0, w.shape[1] - 1] -= c * np.eye(2)
+        out.append(w)
+    return out
+
+
+def test_energy_shift_changes_only_the_global_phase():
+    """The kernels may evolve with H - E*I (E per trajectory); in the method this is a global phase.
+
+    First the finite-state MPO with -c on every on-site channel is H - c*L*I (dense check); then
+    whole truncated TJM trajectories (dynamic TDVP, dissipation, jumps, sampling) with H and with
+    the shifted MPO give the same observables."""
+    L, c = 5, 0.37
+    W = I.xxx_mpo(L, 1.0, 0.5)
+    Ws = _shifted_mpo(W, c)
+    assert np.allclose(O2.mpo_to_dense(Ws), O2.mpo_to_dense(W) - c * L * np.eye(2 ** L), atol=1e-13)
+    jumps, obs = I.noise(L, 0.2, 0.1), I.z_observables(L) + [(2, I.X)]
+    for traj in range(4):
+        vals = []
+        for WW in (W, Ws):
+            prob = O1.Problem(WW, jumps, 0.1, 4, 1e-10)
+            v, st = O1.run_trajectory(prob, O1.product_mps(I.neel(L)), traj, 7, obs, 8, list(range(9)))
+            vals.append(v)
+        assert np.abs(vals[0] - vals[1]).max() < 1e-10, traj
