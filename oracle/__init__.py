@@ -13,4 +13,11 @@ mps_tjm    O1: the MPS tensor jump method in FP64 (dissipative contraction,
            sampling MPS), step by step in the paper's order.
 dense      O2: the same Strang-ordered jump schedule on a dense state vector,
            and O3: the dense Lindblad master equation for small chains.
+
+Pins (tests/test_oracle_pins.py, tests/test_oracle_ensemble.py) fix every part
+against closed forms, library routines on special cases, dense computations or
+exactly solvable limits, with one exception: the TDVP sweep below full bond
+dimension (mps_tjm.Sweeper with truncation) is parity unpinned -- no closed form
+exists; it is checked only by its exactness at full bond dimension and by its
+monotone convergence to the dense evolution as chi_max grows.
 """
