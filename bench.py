@@ -260,12 +260,8 @@ def main():
     ms = e0.elapsed_time(e1)
     s1 = ctx.stats(rid)
     gpu_launches = ctx.launches() - launches0   # trajectory-kernel launches (each preceded by a counter memset)
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * N * L * a.steps / (t_max / 1000.0)
+    from paper_2501_17913_gb300.shard import job_rate
+    value, t_max = job_rate(N * L * a.steps, ms)       # all ranks' units over the slowest rank's time
     fc = s1["flops_contract"] - s0["flops_contract"]
     fd = s1["flops_decomp"] - s0["flops_decomp"]
     peaks = {}

@@ -45,3 +45,20 @@ def merge_ensemble(per_traj_local, group=None):
     mean = first[:-1].reshape(shp) / n
     m2 = _allreduce_sum(((x - mean) ** 2).sum(axis=0), group)
     return mean, np.sqrt(m2 / max(n - 1.0, 1.0) / n)
+
+
+def job_rate(units, ms):
+    """Whole-job throughput across ranks: the units all ranks processed over the slowest rank's time
+    (the job ends when its last rank does).  Returns (units per second, slowest time in ms).
+    Without an initialised process group this is the local rate."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return units / (ms / 1000.0), ms
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(u.item()) / (t_max / 1000.0), t_max

@@ -11,7 +11,7 @@ import socket
 import numpy as np
 import torch.multiprocessing as tmp
 
-from paper_2501_17913_gb300.shard import merge_ensemble, shard_range
+from paper_2501_17913_gb300.shard import job_rate, merge_ensemble, shard_range
 
 
 def _free_port():
@@ -64,3 +64,26 @@ def test_two_rank_merge_equals_single_process(tmp_path):
     merged = np.load(tmp_path / "merged.npy")
     assert np.allclose(merged[0], single.mean(axis=0), atol=1e-15)
     assert np.allclose(merged[1], single.std(axis=0, ddof=1) / np.sqrt(n_total), atol=1e-15)
+
+
+def _rate_main(rank, world, port, outdir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    units, ms = (100.0, 1000.0) if rank == 0 else (300.0, 2000.0)
+    value, t_max = job_rate(units, ms)
+    np.save(os.path.join(outdir, "rate%d.npy" % rank), np.array([value, t_max]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_job_rate_is_all_units_over_the_slowest_rank(tmp_path):
+    """The benchmark's whole-job value under torchrun: sum of units / max of times, on every rank."""
+    world = 2
+    tmp.start_processes(_rate_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                        start_method="spawn")
+    for r in range(world):
+        value, t_max = np.load(tmp_path / ("rate%d.npy" % r))
+        assert t_max == 2000.0 and value == 400.0 / 2.0
+    assert job_rate(50.0, 500.0) == (100.0, 500.0)      # no process group: the local rate
