@@ -37,7 +37,7 @@ enum {
   TJM_EINVAL = 1,     /* invalid argument (sizes, shapes, times off the dt grid, ...) */
   TJM_ENOMEM = 2,     /* device memory exhausted */
   TJM_ENUMERIC = 3,   /* at least one trajectory hit a non-finite or zero norm */
-  TJM_ETIMEOUT = 4,   /* a bounded device wait gave up */
+  TJM_ETIMEOUT = 4,   /* a bounded wait gave up (tjm_wait) */
   TJM_EBUSY = 5,      /* the run is still executing (tjm_poll) */
   TJM_EINTERNAL = 6,  /* library bug or inconsistent state */
   TJM_ECUDA = 7       /* a CUDA runtime call failed; see tjm_last_error */
@@ -47,7 +47,10 @@ enum {
  * baseline).  FP32: tensor contractions and Krylov vectors in complex FP32
  * with FP32 accumulation; QR/SVD in FP64; norms, jump weights, Lanczos
  * coefficients and expectation values accumulated in FP64.  FP32_DEC32: as
- * FP32 but the QR/SVD factorizations also in FP32 (FP64 accumulations kept). */
+ * FP32 but the QR/SVD factorizations also in FP32, in shared memory, with
+ * compensated FP32 reductions in the Jacobi SVD and a Gram-Schmidt pass that
+ * keeps the factors orthonormal to FP32 working precision (the FP64
+ * accumulations listed above are kept). */
 enum { TJM_PREC_FP64 = 0, TJM_PREC_FP32 = 1, TJM_PREC_FP32_DEC32 = 2 };
 
 /* Hamiltonian H0 as a matrix product operator (Methods, Sec. "Matrix product
