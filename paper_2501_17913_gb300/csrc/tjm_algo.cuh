@@ -210,8 +210,9 @@ __device__ void build_right_envs(const Ctx<Tc, Td>& c) {
 // ------------------------------------------------------------------ Lanczos exponential
 // v <- exp(i theta H) v with H given by `kind` (1: one site l, 2: two sites l,l+1,
 // 0: bond l).  Stopping rule: |beta_k [exp(i theta T_k) e_1]_k| < tol or kmax
-// matvecs.  Full re-orthogonalisation: classical Gram-Schmidt, two passes,
-// coefficients in FP64.  Returns the number of matvecs.
+// matvecs.  Full re-orthogonalisation: the three-term recurrence followed by
+// one classical Gram-Schmidt pass over the whole basis, coefficients in FP64.
+// Returns the number of matvecs.
 template <class Tc, class Td>
 __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int chl, int chr, cx<Tc>* v, int n, double theta) {
   const int kmax = c.P->krylov_max;
