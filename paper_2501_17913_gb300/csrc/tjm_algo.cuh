@@ -253,7 +253,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       const cx<Tc>* __restrict__ vkm = kb + (long long)(k > 0 ? k - 1 : 0) * n;
       const Tc bm = k > 0 ? (Tc)beta[k - 1] : (Tc)0;
       Tc ax = 0;
-      #pragma unroll 2
+#pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
         cx<Tc> t = wv[i];
         if (k > 0) { t.x -= bm * vkm[i].x; t.y -= bm * vkm[i].y; }
@@ -273,7 +273,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
         cx<Tc> acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = czero<Tc>();
-        #pragma unroll 2
+#pragma unroll 2
         for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
           cx<Tc> wi = wv[i];
           if (j0 == 0) {   // each thread updates, then rereads, only its own entries
@@ -307,7 +307,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
       for (int j = threadIdx.x; j < nb; j += TJM_THREADS) hw[j] = mk((Tc)hh[2 * j], (Tc)hh[2 * j + 1]);
       __syncthreads();
       Tc n2 = 0;
-      #pragma unroll 2
+#pragma unroll 2
       for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
         cx<Tc> t = wv[i];
 #pragma unroll 4
@@ -339,7 +339,7 @@ __device__ __noinline__ int lanczos(const Ctx<Tc, Td>& c, int kind, int l, int c
   cx<Tc>* cw = reinterpret_cast<cx<Tc>*>(c.red);
   for (int j = threadIdx.x; j < nk; j += TJM_THREADS) cw[j] = mk((Tc)(b0 * cf[j].x), (Tc)(b0 * cf[j].y));
   __syncthreads();
-  #pragma unroll 2
+#pragma unroll 2
   for (int i = threadIdx.x; i < n; i += TJM_THREADS) {
     cx<Tc> acc = czero<Tc>();
     for (int j = 0; j < nk; ++j) cfma(acc, cw[j], c.krylov[(long long)j * n + i]);
