@@ -62,3 +62,28 @@ def job_rate(units, ms):
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     t_max = float(t.item())
     return float(u.item()) / (t_max / 1000.0), t_max
+
+
+class PeerFailure(RuntimeError):
+    """A rank did not report in time: it failed, left or never joined."""
+
+
+def report_alive(store, rank: int, tag: str):
+    """Record in the shared key-value store that this rank reached `tag` (e.g. the end of a step)."""
+    store.set("%s/%d" % (tag, rank), "1")
+
+
+def wait_peers(store, world: int, tag: str, timeout_s: float):
+    """Block until every rank has reported `tag`; raise PeerFailure naming the missing ranks after
+    timeout_s.  Ranks call this between steps, before their next launch, so a rank that died is
+    noticed on the host and no kernel or collective is left waiting on it."""
+    import time
+    deadline = time.monotonic() + timeout_s
+    missing = list(range(world))
+    while True:
+        missing = [r for r in missing if not store.check(["%s/%d" % (tag, r)])]
+        if not missing:
+            return
+        if time.monotonic() >= deadline:
+            raise PeerFailure("ranks %s did not reach %r within %.1f s" % (missing, tag, timeout_s))
+        time.sleep(0.05)

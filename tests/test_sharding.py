@@ -11,7 +11,7 @@ import socket
 import numpy as np
 import torch.multiprocessing as tmp
 
-from paper_2501_17913_gb300.shard import job_rate, merge_ensemble, shard_range
+from paper_2501_17913_gb300.shard import PeerFailure, job_rate, merge_ensemble, report_alive, shard_range, wait_peers
 
 
 def _free_port():
@@ -87,3 +87,31 @@ def test_job_rate_is_all_units_over_the_slowest_rank(tmp_path):
         value, t_max = np.load(tmp_path / ("rate%d.npy" % r))
         assert t_max == 2000.0 and value == 400.0 / 2.0
     assert job_rate(50.0, 500.0) == (100.0, 500.0)      # no process group: the local rate
+
+
+def _heartbeat_main(rank, world, port, outdir):
+    from datetime import timedelta
+
+    import torch.distributed as dist
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=timedelta(seconds=30))
+    report_alive(store, rank, "step0")
+    wait_peers(store, world, "step0", 20.0)          # every rank finishes step 0
+    if rank == 1:
+        return                                        # rank 1 leaves between steps (a failed rank)
+    report_alive(store, rank, "step1")
+    try:
+        wait_peers(store, world, "step1", 2.0)
+        result = "no failure seen"
+    except PeerFailure as e:
+        result = str(e)
+    with open(os.path.join(outdir, "rank0.txt"), "w") as f:
+        f.write(result)
+
+
+def test_a_rank_that_leaves_is_noticed_on_the_host(tmp_path):
+    """Failure detection without any device fault: the surviving rank learns from the store, before
+    its next launch, that rank 1 is gone."""
+    tmp.start_processes(_heartbeat_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True,
+                        start_method="spawn")
+    msg = open(tmp_path / "rank0.txt").read()
+    assert "ranks [1]" in msg and "step1" in msg
