@@ -70,3 +70,34 @@ def test_invalid_problems_rejected_before_any_device_call(lib, case):
     with pytest.raises(tjm.TJMError) as e:
         tjm.Context(W, I.noise(len(W), 0.1, 0.1), dt, chi, eps, **kw)
     assert e.value.status == tjm.TJM_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's sizes and field offsets (a C program
+    compiled against include/tjm.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"tjm_mpo": tjm.tjm_mpo, "tjm_jump": tjm.tjm_jump, "tjm_observable": tjm.tjm_observable,
+               "tjm_state": tjm.tjm_state, "tjm_options": tjm.tjm_options, "tjm_stats": tjm.tjm_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tjm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f[0], name, f[0]))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        got = C.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
