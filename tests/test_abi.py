@@ -101,3 +101,13 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got == int(value), (name, field, got, value)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_complex_marshalling_is_interleaved_row_major():
+    """Operators and states cross the ABI as interleaved (re, im) doubles, row-major (tjm.h)."""
+    op = np.array([[1 + 2j, 3 - 4j], [5j, -6.0]])
+    assert list(tjm._op8(op)) == [1, 2, 3, -4, 0, 5, -6, 0]
+    site = np.arange(12).reshape(2, 2, 3) * (1 + 1j)
+    flat = tjm._cplx(site)
+    assert flat.shape == (24,) and np.array_equal(flat[0::2], site.real.ravel()) and \
+        np.array_equal(flat[1::2], site.imag.ravel())
