@@ -3,9 +3,9 @@
 Calls only the CPU oracle (oracle/) and the input generator; nothing here
 comes from the CUDA path.  Usage:
 
-    python tests/golden/make_golden.py l30      # L=30, chi=32: 8 sampled trajectories, all 100 steps
-    python tests/golden/make_golden.py l1000    # L=1000, chi=64 from Neel: 2 sampled trajectories, 3 steps
-    python tests/golden/make_golden.py bench    # the benchmark workload (random chi=64 MPS): trajectory 0, 1 step
+    python tests/golden/make_golden.py l30      # L=30, chi=32: 32 sampled trajectories, all 100 steps
+    python tests/golden/make_golden.py l1000    # L=1000, chi=64 from Neel: 8 sampled trajectories, 3 steps
+    python tests/golden/make_golden.py bench    # the benchmark workload (random chi=64 MPS): 4 trajectories, 1 step
 """
 import os
 import sys
@@ -22,15 +22,15 @@ from oracle_jobs import run_traj  # noqa: E402
 
 SETS = {
     # name: (workload factory, kwargs, sampled global trajectory ids, options)
-    "l30": ("config_l30", {}, [0, 137, 274, 411, 548, 685, 822, 959], {}),
-    "l1000": ("config_l1000", {}, [0, 201], {"n_steps": 3}),
-    "bench": ("config_bench", {}, [0], {"n_steps": 1}),
+    "l30": ("config_l30", {}, sorted([0, 137, 274, 411, 548, 685, 822, 959] + list(range(20, 1024, 43))), {}),
+    "l1000": ("config_l1000", {}, [0, 33, 67, 101, 150, 201, 230, 255], {"n_steps": 3}),
+    "bench": ("config_bench", {}, [0, 64, 128, 192], {"n_steps": 1}),
 }
 
 
 def make(name):
     fac, kw, trajs, opts = SETS[name]
-    with oracle_pool(min(8, len(trajs))) as pool:
+    with oracle_pool(min(os.cpu_count() or 1, 16, len(trajs))) as pool:
         res = pool.map(run_traj, [(fac, kw, t, opts) for t in trajs])
     vals = np.array([r[0] for r in res])
     m1 = np.array([r[1]["min_margin1"] for r in res])
