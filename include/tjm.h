@@ -43,15 +43,25 @@ enum {
   TJM_ECUDA = 7       /* a CUDA runtime call failed; see tjm_last_error */
 };
 
-/* Arithmetic of the GPU path.  FP64: everything in double (the plain FP64
- * baseline).  FP32: tensor contractions and Krylov vectors in complex FP32
- * with FP32 accumulation; QR/SVD in FP64; norms, jump weights, Lanczos
- * coefficients and expectation values accumulated in FP64.  FP32_DEC32: as
- * FP32 but the QR/SVD factorizations also in FP32, in shared memory, with
- * compensated FP32 reductions in the Jacobi SVD and a Gram-Schmidt pass that
- * keeps the factors orthonormal to FP32 working precision (the FP64
- * accumulations listed above are kept). */
-enum { TJM_PREC_FP64 = 0, TJM_PREC_FP32 = 1, TJM_PREC_FP32_DEC32 = 2 };
+/* Arithmetic of the GPU path (the precision plan: contractions in FP32, the
+ * QR/SVD truncations, norms, jump probabilities and Lanczos coefficients in
+ * FP64).
+ *   FP64        everything in double (the plain FP64 baseline).
+ *   FP32        tensor contractions and Krylov vectors in complex FP32 with
+ *               FP32 accumulation; QR and SVD in native FP64; norms, jump
+ *               weights, Lanczos coefficients and expectation values
+ *               accumulated in FP64.
+ *   FP32_DEC32  as FP32 but QR and SVD in FP32, in shared memory, with
+ *               compensated FP32 reductions in the Jacobi SVD and a
+ *               Gram-Schmidt pass that keeps the factors orthonormal to FP32
+ *               working precision (a stated-error mode).
+ *   FP32_DF64   (default) as FP32 with QR and SVD in emulated FP64:
+ *               double-float numbers (pairs of FP32 carrying a 48-bit
+ *               significand) on the FP32 pipes.  GB300 executes 2 native FP64
+ *               FMAs per clock per SM against 128 FP32 FMAs; the emulation
+ *               gives the FP64 factorizations about 3x the native rate with
+ *               results equal to native FP64 to ~1e-13. */
+enum { TJM_PREC_FP64 = 0, TJM_PREC_FP32 = 1, TJM_PREC_FP32_DEC32 = 2, TJM_PREC_FP32_DF64 = 3 };
 
 /* Hamiltonian H0 as a matrix product operator (Methods, Sec. "Matrix product
  * (density) operators"; Sec. "Initialization" item 2).  D[0..L] are the MPO
@@ -92,7 +102,7 @@ typedef struct {
 } tjm_state;
 
 typedef struct {
-  int precision;        /* TJM_PREC_*; default TJM_PREC_FP32 */
+  int precision;        /* TJM_PREC_*; default TJM_PREC_FP32_DF64 */
   int krylov_max;       /* Lanczos iterations per exponential, <= 30; default 30 */
   double krylov_tol;    /* Lanczos a-posteriori error tolerance; default 1e-12 (FP64) / 1e-7 (FP32) */
   int exact_full_bond;  /* 1: pad product states to full bond dimension, never truncate */
@@ -198,7 +208,10 @@ tjm_status tjm_run_bonds(tjm_ctx* ctx, int64_t run_id, int* chi);
  * run: its completed step count, bond dimensions chi [L + 1] and site tensors
  * packed as in tjm_state (site l is [chi[l]][d][chi[l+1]] complex; data must
  * hold sum_l chi[l]*d*chi[l+1] complex numbers, at most L*d*64*64).  The
- * state is the sampling MPS Phi_j after step j (Sec. "Algorithm"). */
+ * state is the sampling MPS Phi_j after step j (Sec. "Algorithm").
+ * TJM_EBUSY (nothing copied) while the trajectory sits between the halves of
+ * a phase-wise step (after tjm_run_advance(-1), before -2): it then holds
+ * X = U[dt] Phi_j, which is not a state a run can resume from. */
 tjm_status tjm_run_get_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int* step, int* chi, double* data);
 
 /* tjm_run_set_state -- overwrite trajectory `traj` of a run with an MPS in
@@ -241,8 +254,9 @@ int64_t tjm_launch_count(const tjm_ctx* ctx);
 /* ------------------------------------------------------------------------
  * Kernel-level self tests: one CTA runs one building block of the trajectory
  * kernel on one small problem.  Matrices are row-major complex interleaved;
- * double_precision selects the FP64 (1) or FP32 (0) instantiation.  They
- * allocate their own device memory and synchronise the device.
+ * double_precision selects the FP32 (0), FP64 (1) or double-float emulated
+ * FP64 (2) instantiation.  They allocate their own device memory and
+ * synchronise the device.
  * ---------------------------------------------------------------------- */
 
 /* Householder QR of A (m x n, m, n <= 256): Q (m x k) with orthonormal
@@ -255,6 +269,17 @@ tjm_status tjm_selftest_qr(int double_precision, int m, int n, const double* A, 
  * exactly-zero singular values are completed to an orthonormal set.  Used for
  * the truncations of Sec. "1TDVP and 2TDVP as tensor networks". */
 tjm_status tjm_selftest_svd(int double_precision, int m, int n, const double* A, double* U, double* S, double* V);
+
+/* C = op(A) op(B) on the tensor cores (tcgen05, TF32 inputs with the 3xTF32
+ * split, FP32 accumulation in tensor memory), one CTA: the complex GEMM of
+ * the effective-Hamiltonian and environment contractions (Fig. 2 networks).
+ * A is M x K and B is K x N, row-major complex doubles rounded to FP32 on the
+ * device; conj_a / conj_b conjugate them; a_col_major / b_k_contig store the
+ * operands transposed on the device first, so both access patterns of the
+ * GEMM are exercised.  C (M x N) is returned as doubles.  M, N, K <= 1024.
+ * TJM_ETIMEOUT if the kernel's bounded wait for the tensor cores ran out. */
+tjm_status tjm_selftest_tc_cgemm(int M, int N, int K, int conj_a, int conj_b, int a_col_major, int b_k_contig,
+                                 const double* A, const double* B, double* C);
 
 /* exp(i theta T) e_1 for the k x k (k <= 32) real symmetric tridiagonal
  * T = tridiag(beta, alpha, beta): the Lanczos exponential's small factor
@@ -274,7 +299,8 @@ tjm_status tjm_selftest_philox(uint64_t seed, const uint64_t* traj, const uint32
  * latency-sensitive loops that must not pay for cudaMalloc/cudaFree (cudaFree
  * synchronises the whole device).
  *
- * tjm_svd_noalloc -- the same one-CTA Jacobi SVD as tjm_selftest_svd, with
+ * tjm_svd_noalloc -- the same one-CTA Jacobi SVD as tjm_selftest_svd (same
+ * kernel body; double_precision 0 FP32, 1 FP64, 2 double-float), with
  * DEVICE pointers: A (m x n), U (m x nn), S (nn), V (n x nn), nn = min(m, n),
  * row-major complex interleaved doubles (S real), A = U diag(S) V^H, S
  * descending.  The caller owns and provides all four buffers; the call
@@ -288,7 +314,9 @@ tjm_status tjm_selftest_philox(uint64_t seed, const uint64_t* traj, const uint32
  * Every call on a device shares the one workspace and leaves its contents
  * behind (nothing in it needs clearing): calls whose kernels overlap on the
  * GPU (different streams without ordering) race and corrupt each other.
- * Returns TJM_ECUDA if the launch fails. */
+ * Returns TJM_ECUDA if the launch fails, and also, without launching, if
+ * a CUDA error from earlier work is already pending (that error is left in
+ * place for the caller to read). */
 #define TJM_NOALLOC_MAX_DIM 128
 tjm_status tjm_svd_noalloc(int double_precision, int m, int n, const double* A, double* U, double* S, double* V,
                            void* stream);

@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library libtjm.so for GB300 (sm_103a) with nvcc.
 
-The three precision instantiations of the trajectory kernel and the host
+The four precision instantiations of the trajectory kernel and the host
 runtime are separate translation units compiled in parallel, then linked into
 one shared library next to this file.
 """
@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtjm.so")
-SOURCES = ["tjm_capi.cu", "tjm_kernel_f64.cu", "tjm_kernel_f32.cu", "tjm_kernel_f32d32.cu", "tjm_selftest.cu",
+SOURCES = ["tjm_capi.cu", "tjm_kernel_f64.cu", "tjm_kernel_f32.cu", "tjm_kernel_f32d32.cu", "tjm_kernel_f32df.cu",
+           "tjm_selftest.cu",
            "tjm_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

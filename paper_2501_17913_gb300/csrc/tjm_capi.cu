@@ -168,7 +168,7 @@ void expm_neg_herm2(const zc A[4], double s, zc out[4]) {
 }
 
 size_t szc_of(int prec) { return prec == TJM_PREC_FP64 ? 16 : 8; }
-size_t szd_of(int prec) { return prec == TJM_PREC_FP32_DEC32 ? 8 : 16; }
+size_t szd_of(int prec) { return prec == TJM_PREC_FP32_DEC32 ? 8 : 16; }   // df64 is 8 bytes like double
 
 // Full bond dimension of bond b in an L-site d=2 chain.
 int full_dim(int L, int b) {
@@ -217,6 +217,7 @@ int resident(tjm_ctx* ctx) {
   switch (ctx->opt.precision) {
     case TJM_PREC_FP64: per_sm = tjm::occupancy_f64(); break;
     case TJM_PREC_FP32_DEC32: per_sm = tjm::occupancy_f32d32(); break;
+    case TJM_PREC_FP32_DF64: per_sm = tjm::occupancy_f32df(); break;
     default: per_sm = tjm::occupancy_f32(); break;
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -257,7 +258,7 @@ extern "C" {
 
 void tjm_default_options(tjm_options* o) {
   if (!o) return;
-  o->precision = TJM_PREC_FP32;
+  o->precision = TJM_PREC_FP32_DF64;
   o->krylov_max = 30;
   o->krylov_tol = 0.0;   // 0: precision default
   o->exact_full_bond = 0;
@@ -280,7 +281,7 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   tjm_default_options(&ctx->opt);
   if (opts) ctx->opt = *opts;
   tjm_options& o = ctx->opt;
-  if (o.precision < 0 || o.precision > 2) return fail(nullptr, TJM_EINVAL, "");
+  if (o.precision < 0 || o.precision > 3) return fail(nullptr, TJM_EINVAL, "");
   if (o.tile_rule < 0 || o.tile_rule > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.krylov_max <= 0 || o.krylov_max > 30) o.krylov_max = 30;
   if (!(o.krylov_tol > 0)) o.krylov_tol = o.precision == TJM_PREC_FP64 ? 1e-12 : 1e-7;
@@ -648,6 +649,10 @@ static tjm_status launch(tjm_ctx* ctx, tjm::SlotDev* const* order, int n, int* n
       e = tjm::launch_f32d32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
                              ctx->scratch_stride, ctx->sdims);
       break;
+    case TJM_PREC_FP32_DF64:
+      e = tjm::launch_f32df(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
+                            ctx->scratch_stride, ctx->sdims);
+      break;
     default:
       e = tjm::launch_f32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
                           ctx->sdims);
@@ -868,6 +873,12 @@ tjm_status tjm_run_get_state(tjm_ctx* ctx, int64_t run_id, int64_t traj, int* st
   TJM_CU(cudaEventSynchronize(R->done));
   tjm::SlotDev S;
   TJM_CU(cudaMemcpy(&S, R->slots + traj, sizeof S, cudaMemcpyDeviceToHost));
+  // Between the two halves of a phase-wise step (U[dt] applied, D and J not
+  // yet) the held MPS is X, not a sampling MPS Phi_j: a checkpoint taken there
+  // would be resumed as Phi_j and apply U[dt] twice.
+  if (S.flags & 2)
+    return fail(ctx, TJM_EBUSY, "trajectory %lld is between U[dt] and D/J of a step (advance -2 first)",
+                (long long)traj);
   if (step) *step = S.step;
   const int L = R->L;
   TJM_CU(cudaMemcpy(chi, S.chi, (L + 1) * sizeof(int), cudaMemcpyDeviceToHost));

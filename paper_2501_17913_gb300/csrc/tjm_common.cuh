@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tjm_df64.cuh"
+
 #ifndef TJM_THREADS
 #define TJM_THREADS 256
 #endif
@@ -94,6 +96,21 @@ __device__ __forceinline__ void grp8_sum_acc2(float& v0, float& v1, unsigned m) 
     b = df_add(b, {__shfl_xor_sync(m, b.hi, o), __shfl_xor_sync(m, b.lo, o)});
   }
   v0 = a.hi + a.lo; v1 = b.hi + b.lo;
+}
+
+// double-float versions: both words are shuffled, partners added with the
+// accurate double-word adder
+__device__ __forceinline__ df64 grp8_sum(df64 v, unsigned m) {
+  for (int o = 4; o > 0; o >>= 1) v = v + shfl_xor_df(m, v, o);
+  return v;
+}
+__device__ __forceinline__ void grp8_sum_acc2(df64& v0, df64& v1, unsigned m) {
+  v0 = grp8_sum(v0, m);
+  v1 = grp8_sum(v1, m);
+}
+__device__ __forceinline__ df64 warp_sum(df64 v) {
+  for (int o = 16; o > 0; o >>= 1) v = v + shfl_xor_df(0xffffffffu, v, o);
+  return v;
 }
 
 __device__ __forceinline__ double warp_max(double v) {

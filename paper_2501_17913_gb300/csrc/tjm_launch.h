@@ -16,5 +16,6 @@ namespace tjm {
 TJM_DECLARE_LAUNCH(f64)
 TJM_DECLARE_LAUNCH(f32)
 TJM_DECLARE_LAUNCH(f32d32)
+TJM_DECLARE_LAUNCH(f32df)
 
 }  // namespace tjm

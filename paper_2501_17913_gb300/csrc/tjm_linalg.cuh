@@ -18,6 +18,18 @@ namespace tjm {
 template <class T> struct eps_of;
 template <> struct eps_of<float> { static constexpr double v = 1.1920928955078125e-07; };
 template <> struct eps_of<double> { static constexpr double v = 2.220446049250313e-16; };
+// double-float: a few units of 2^-48 per operation (tjm_df64.cuh); 2^-46 bounds them
+template <> struct eps_of<df64> { static constexpr double v = 1.4210854715202004e-14; };
+
+// |z| without squaring z: max(|x|, |y|) sqrt(1 + (min / max)^2).
+template <class T>
+__device__ __forceinline__ T cabs_scaled(cx<T> z) {
+  const T ax = fabs(z.x), ay = fabs(z.y);
+  const T m = ax > ay ? ax : ay;
+  if (!(m > T(0))) return T(0);
+  const T rx = ax / m, ry = ay / m;
+  return m * sqrt(rx * rx + ry * ry);
+}
 
 // ------------------------------------------------------------------ QR
 // x[:, c] <- (I - tau v v^H) x[:, c] for columns c0 <= c < c1 of x (column-major,
@@ -46,7 +58,7 @@ __device__ __forceinline__ void grp_reflect(int m, int j, const cx<T>* v, T tj, 
     s.x = grp8_sum(s.x, gmask);
     s.y = grp8_sum(s.y, gmask);
     const cx<T> f = mk(-tj * s.x, -tj * s.y);
-    T q2 = 0;
+    T q2 = T(0);
     for (int t = gl, i = i0; t < len; t += 8) {
       cx<T> y = xc[i];
       cfma(y, f, v[i]);
@@ -83,7 +95,7 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
   const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3;
   const unsigned gmask = 0xffu << ((threadIdx.x & 31) & 24);
   if (threadIdx.x < 8) {
-    T s2 = 0;
+    T s2 = T(0);
     for (int i = threadIdx.x; i < m; i += 8) s2 += norm2(a[i]);
     s2 = grp8_sum(s2, 0xffu);
     if (threadIdx.x == 0) cn[0] = s2;
@@ -113,7 +125,7 @@ __device__ __noinline__ void blk_qr(int m, int n, cx<T>* a, cx<T>* q, cx<T>* r, 
       grp_reflect<T>(m, j, col, tj, a, j + 1, n, nx);
     } else if (nx && grp == 0) {
       const cx<T>* xc = a + (long long)(j + 1) * m;
-      T s2 = 0;
+      T s2 = T(0);
       for (int i = j + 1 + gl; i < m; i += 8) s2 += norm2(xc[i]);
       s2 = grp8_sum(s2, gmask);
       if (gl == 0) *nx = s2;
@@ -187,7 +199,7 @@ __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* p
       // one aligned group of 8 lanes per projection
       for (int o = grp; o < c; o += TJM_THREADS / 8) {
         const cx<T>* qo = q + (long long)perm[o] * len;
-        T hx = 0, hy = 0;
+        T hx = T(0), hy = T(0);
         for (int i = gl; i < len; i += 8) {
           const cx<T> x = qo[i], y = qc[i];
           hx = fma(x.x, y.x, fma(x.y, y.y, hx));
@@ -207,7 +219,7 @@ __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* p
         qc[i] = a;
       }
     }
-    T nr = 0;
+    T nr = T(0);
     for (int i = threadIdx.x; i < len; i += TJM_THREADS) nr += norm2(qc[i]);
     nr = blk_sum_pos(nr, red);
     const T f = nr > (T)0 ? (T)1 / sqrt(nr) : (T)0;
@@ -264,7 +276,7 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         if (p >= nn || qq >= nn) continue;
         cx<T>* ap = a + (long long)p * mm;
         cx<T>* aq = a + (long long)qq * mm;
-        T al0 = 0, be0 = 0;
+        T al0 = T(0), be0 = T(0);
         cx<T> ga0 = czero<T>();
         for (int r = gl, i = ia0; r < mm; r += 8) {
           const cx<T> x = ap[i], y = aq[i];
@@ -281,8 +293,11 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
           if (be <= negl && be != (T)0) for (int i = gl; i < mm; i += 8) aq[i] = czero<T>();
           continue;
         }
-        const T ag = sqrt(norm2(ga));
-        if (!(ag > tol * sqrt(al * be))) continue;
+        // |ga| and the test scaled so that no product of two squared norms is formed: in double-float
+        // (FP32 exponent range) |ga|^2 and al * be of noise-level columns underflow, and a phase
+        // ga / |ga| computed from underflowed values is not unitary
+        const T ag = cabs_scaled(ga);
+        if (!(ag > tol * sqrt(al) * sqrt(be))) continue;
         const T zeta = (be - al) / ((T)2 * ag);
         const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
         const T c = (T)1 / sqrt((T)1 + t * t), sn = c * t;
@@ -328,7 +343,7 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
   __syncthreads();
   for (int e = threadIdx.x; e < nn; e += TJM_THREADS) s[e] = sv[iw[e]];
   const bool f32 = sizeof(T) == 4;
-  if (f32) {
+  if constexpr (sizeof(T) == 4) {
     // In FP32 the converged columns are orthogonal only to tol (about 5e-7)
     // and the accumulated rotations drift by a similar amount; sites cut from
     // U or V must be isometries to working precision, because every
@@ -369,14 +384,15 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
           double hx = 0.0, hy = 0.0;
           for (int i = threadIdx.x; i < mm; i += TJM_THREADS) {
             const cx<T> x = uo[i], y = uc[i];
-            hx += (double)x.x * y.x + (double)x.y * y.y;
-            hy += (double)x.x * y.y - (double)x.y * y.x;
+            hx += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
+            hy += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
           }
           hx = blk_sum(hx, red);
           hy = blk_sum(hy, red);
           for (int i = threadIdx.x; i < mm; i += TJM_THREADS) {
             const cx<T> x = uo[i];
-            uc[i] = uc[i] - mk((T)(hx * x.x - hy * x.y), (T)(hx * x.y + hy * x.x));
+            const double xr = (double)x.x, xi = (double)x.y;
+            uc[i] = uc[i] - mk((T)(hx * xr - hy * xi), (T)(hx * xi + hy * xr));
           }
           __syncthreads();
         }

@@ -12,18 +12,18 @@
 #include <mutex>
 
 #include "tjm.h"
-#include "tjm_linalg.cuh"
+#include "tjm_svd_call.cuh"
 
 namespace {
 
 constexpr int kMaxDim = TJM_NOALLOC_MAX_DIM;
-// workspace of the largest problem (FP64): work matrix, U, V, the rotation
-// accumulator with its singular-value tail, the singular values, and the
-// permutation ints -- identical to the per-call layout of the SVD self test
-constexpr size_t kComplexSlots = (size_t)2 * kMaxDim * kMaxDim + 2 * kMaxDim * kMaxDim + 4 * kMaxDim + 8;
-constexpr size_t kWorkBytes = kComplexSlots * 16;
+// workspace of the largest problem (a 128 x 128 work matrix, 16-byte complex
+// elements for FP64 and double-float, 8 for FP32), laid out and sized by the
+// same function as every other standalone SVD call, plus the permutation ints
+constexpr size_t kWorkBytes = (tjm::svd_call_slots(kMaxDim, kMaxDim) * 16 + 255) / 256 * 256;
 constexpr size_t kIntBytes = (size_t)2 * kMaxDim * sizeof(int);
 constexpr size_t kScratchBytes = kWorkBytes + kIntBytes;
+static_assert(kWorkBytes >= tjm::svd_call_slots(kMaxDim, kMaxDim) * 16, "workspace holds the largest call");
 
 // Held by every GPU that loads the library, for the life of the process.
 static __device__ __align__(256) unsigned char g_svd_scratch[kScratchBytes];
@@ -37,38 +37,16 @@ __global__ void __launch_bounds__(TJM_THREADS, 1)
 svd_noalloc_kernel(int m, int n, const tjm::cx<double>* A, tjm::cx<double>* U, double* S, tjm::cx<double>* V,
                    tjm::cx<T>* ws, int* iw) {
   __shared__ double red[TJM_WARPS * 64];
-  const bool tr = m < n;
-  const int mm = tr ? n : m, nn = tr ? m : n;
-  tjm::cx<T>* a = ws;
-  tjm::cx<T>* u = a + mm * nn;
-  tjm::cx<T>* v = u + mm * nn;
-  tjm::cx<T>* vw = v + nn * nn;
-  T* s = reinterpret_cast<T*>(vw + nn * nn + 2 * nn);
-  // every workspace entry the factorization reads is written here or inside
-  // blk_svd_jacobi first, so nothing has to be cleared between calls
-  for (int e = threadIdx.x; e < mm * nn; e += TJM_THREADS) {
-    const int i = e % mm, j = e / mm;
-    a[e] = tr ? tjm::cvt<T>(tjm::conj(A[j * n + i])) : tjm::cvt<T>(A[i * n + j]);
-  }
-  __syncthreads();
-  tjm::blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, reinterpret_cast<T*>(vw + nn * nn), iw, red, true);
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * nn; e += TJM_THREADS) {
-    const int i = e / nn, j = e % nn;
-    U[e] = tjm::cvt<double>(tr ? v[j * nn + i] : u[j * mm + i]);
-  }
-  for (int e = threadIdx.x; e < n * nn; e += TJM_THREADS) {
-    const int i = e / nn, j = e % nn;
-    V[e] = tjm::cvt<double>(tr ? u[j * mm + i] : v[j * nn + i]);
-  }
-  for (int e = threadIdx.x; e < nn; e += TJM_THREADS) S[e] = (double)s[e];
+  // nothing in the workspace has to be cleared between calls: every entry the
+  // factorization reads is written first within the call
+  tjm::svd_call_body<T>(m, n, A, U, S, V, ws, iw, red);
 }
 
 }  // namespace
 
 extern "C" tjm_status tjm_svd_noalloc(int double_precision, int m, int n, const double* A, double* U, double* S,
                                       double* V, void* stream) {
-  if (m < 1 || n < 1 || !A || !U || !S || !V) return TJM_EINVAL;
+  if (m < 1 || n < 1 || !A || !U || !S || !V || double_precision < 0 || double_precision > 2) return TJM_EINVAL;
   if (m > kMaxDim || n > kMaxDim) return TJM_EINVAL;   // the static workspace holds at most 128 x 128
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TJM_ECUDA;
@@ -90,11 +68,22 @@ extern "C" tjm_status tjm_svd_noalloc(int double_precision, int m, int n, const 
   const auto* dA = reinterpret_cast<const tjm::cx<double>*>(A);
   auto* dU = reinterpret_cast<tjm::cx<double>*>(U);
   auto* dV = reinterpret_cast<tjm::cx<double>*>(V);
-  if (double_precision)
+  // An error the caller left pending is not ours to consume: report it
+  // without launching and leave it in place.
+  if (cudaPeekAtLastError() != cudaSuccess) return TJM_ECUDA;
+  if (double_precision == 2)
+    svd_noalloc_kernel<tjm::df64><<<1, TJM_THREADS, 0, st>>>(m, n, dA, dU, S, dV,
+                                                             reinterpret_cast<tjm::cx<tjm::df64>*>(scratch), iw);
+  else if (double_precision)
     svd_noalloc_kernel<double><<<1, TJM_THREADS, 0, st>>>(m, n, dA, dU, S, dV,
                                                            reinterpret_cast<tjm::cx<double>*>(scratch), iw);
   else
     svd_noalloc_kernel<float><<<1, TJM_THREADS, 0, st>>>(m, n, dA, dU, S, dV,
                                                           reinterpret_cast<tjm::cx<float>*>(scratch), iw);
-  return cudaGetLastError() == cudaSuccess ? TJM_OK : TJM_ECUDA;
+  // nothing was pending before the launch, so an error now is the launch's own
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return TJM_ECUDA;
+  }
+  return TJM_OK;
 }

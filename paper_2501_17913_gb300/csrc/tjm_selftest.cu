@@ -7,6 +7,8 @@
 
 #include "tjm.h"
 #include "tjm_linalg.cuh"
+#include "tjm_svd_call.cuh"
+#include "tjm_tc.cuh"
 
 namespace tjm {
 
@@ -41,30 +43,37 @@ template <class T>
 __global__ void __launch_bounds__(TJM_THREADS, 1)
 svd_test_kernel(int m, int n, const cx<double>* A, cx<double>* U, double* S, cx<double>* V, cx<T>* ws, int* iw) {
   __shared__ double red[TJM_WARPS * 64];
-  const bool tr = m < n;
-  const int mm = tr ? n : m, nn = tr ? m : n;
-  cx<T>* a = ws;
-  cx<T>* u = a + mm * nn;
-  cx<T>* v = u + mm * nn;
-  cx<T>* vw = v + nn * nn;
-  T* s = reinterpret_cast<T*>(vw + nn * nn + 2 * nn);
-  for (int e = threadIdx.x; e < mm * nn; e += TJM_THREADS) {
-    const int i = e % mm, j = e / mm;
-    a[e] = tr ? cvt<T>(conj(A[j * n + i])) : cvt<T>(A[i * n + j]);
+  svd_call_body<T>(m, n, A, U, S, V, ws, iw, red);
+}
+
+// C = op(A) op(B) on the tensor cores, one CTA.  A is given row-major M x K,
+// B row-major K x N (complex double, converted to float); a_cm / b_kc store
+// them column-major (A's i index contiguous) / K-contiguous first, so both
+// operand access patterns of the GEMM are exercised.
+__global__ void __launch_bounds__(TJM_THREADS, 1)
+tc_cgemm_test_kernel(int M, int N, int K, int ca, int cb, int a_cm, int b_kc, const cx<double>* A,
+                     const cx<double>* B, cx<double>* C, cx<float>* fa, cx<float>* fb, cx<float>* fc, int* ok) {
+  extern __shared__ __align__(1024) char dsm[];
+  __shared__ tc::Ctl ctl;
+  char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  for (int e = threadIdx.x; e < M * K; e += TJM_THREADS) {
+    const int i = e / K, k = e % K;
+    fa[a_cm ? k * M + i : e] = cvt<float>(A[e]);
+  }
+  for (int e = threadIdx.x; e < K * N; e += TJM_THREADS) {
+    const int k = e / N, j = e % N;
+    fb[b_kc ? j * K + k : e] = cvt<float>(B[e]);
   }
   __syncthreads();
-  blk_svd_jacobi<T>(mm, nn, a, u, s, v, vw, reinterpret_cast<T*>(vw + nn * nn), iw, red, true);
-  __syncthreads();
-  // A = Uw S Vw^H (or its adjoint): return U (m x nn), V (n x nn) row-major
-  for (int e = threadIdx.x; e < m * nn; e += TJM_THREADS) {
-    const int i = e / nn, j = e % nn;
-    U[e] = cvt<double>(tr ? v[j * nn + i] : u[j * mm + i]);
-  }
-  for (int e = threadIdx.x; e < n * nn; e += TJM_THREADS) {
-    const int i = e / nn, j = e % nn;
-    V[e] = cvt<double>(tr ? u[j * mm + i] : v[j * nn + i]);
-  }
-  for (int e = threadIdx.x; e < nn; e += TJM_THREADS) S[e] = (double)s[e];
+  tc::cta_setup(&ctl, 1);
+  tc::TcA ta = {};
+  ta.p = fa; ta.si = a_cm ? 1 : K; ta.sk = a_cm ? M : 1; ta.conj = ca;
+  tc::TcB tb = {};
+  tb.p = fb; tb.sk = b_kc ? 1 : N; tb.sj = b_kc ? K : 1; tb.conj = cb;
+  const bool good = tc::cgemm(&ctl, M, N, K, mk(1.f, 0.f), ta, tb, fc, N, 1, false, smem);
+  tc::cta_teardown(&ctl);
+  for (int e = threadIdx.x; e < M * N; e += TJM_THREADS) C[e] = cvt<double>(fc[e]);
+  if (threadIdx.x == 0) *ok = good ? 1 : 0;
 }
 
 __global__ void expm_test_kernel(int k, const double* alpha, const double* beta, double theta, cx<double>* c) {
@@ -111,7 +120,9 @@ tjm_status tjm_selftest_qr(int double_precision, int m, int n, const double* A, 
   char* ws = d.get<char>((size_t)(m * n + m * k + k * n + 2 * k + 8) * 16);
   if (!dA || !dQ || !dR || !ws) return TJM_ENOMEM;
   if (cudaMemcpy(dA, A, (size_t)m * n * 16, cudaMemcpyHostToDevice) != cudaSuccess) return TJM_ECUDA;
-  if (double_precision)
+  if (double_precision == 2)
+    tjm::qr_test_kernel<tjm::df64><<<1, TJM_THREADS>>>(m, n, dA, dQ, dR, reinterpret_cast<tjm::cx<tjm::df64>*>(ws));
+  else if (double_precision)
     tjm::qr_test_kernel<double><<<1, TJM_THREADS>>>(m, n, dA, dQ, dR, reinterpret_cast<tjm::cx<double>*>(ws));
   else
     tjm::qr_test_kernel<float><<<1, TJM_THREADS>>>(m, n, dA, dQ, dR, reinterpret_cast<tjm::cx<float>*>(ws));
@@ -129,11 +140,14 @@ tjm_status tjm_selftest_svd(int double_precision, int m, int n, const double* A,
   auto* dU = d.get<tjm::cx<double>>(m * nn);
   auto* dV = d.get<tjm::cx<double>>(n * nn);
   auto* dS = d.get<double>(nn);
-  char* ws = d.get<char>((size_t)(2 * mm * nn + 2 * nn * nn + 4 * nn + 8) * 16);
+  char* ws = d.get<char>(tjm::svd_call_slots(mm, nn) * 16);
   int* iw = d.get<int>(2 * nn);
   if (!dA || !dU || !dV || !dS || !ws || !iw) return TJM_ENOMEM;
   if (cudaMemcpy(dA, A, (size_t)m * n * 16, cudaMemcpyHostToDevice) != cudaSuccess) return TJM_ECUDA;
-  if (double_precision)
+  if (double_precision == 2)
+    tjm::svd_test_kernel<tjm::df64><<<1, TJM_THREADS>>>(m, n, dA, dU, dS, dV,
+                                                        reinterpret_cast<tjm::cx<tjm::df64>*>(ws), iw);
+  else if (double_precision)
     tjm::svd_test_kernel<double><<<1, TJM_THREADS>>>(m, n, dA, dU, dS, dV, reinterpret_cast<tjm::cx<double>*>(ws), iw);
   else
     tjm::svd_test_kernel<float><<<1, TJM_THREADS>>>(m, n, dA, dU, dS, dV, reinterpret_cast<tjm::cx<float>*>(ws), iw);
@@ -142,6 +156,33 @@ tjm_status tjm_selftest_svd(int double_precision, int m, int n, const double* A,
   cudaMemcpy(V, dV, (size_t)n * nn * 16, cudaMemcpyDeviceToHost);
   cudaMemcpy(S, dS, (size_t)nn * 8, cudaMemcpyDeviceToHost);
   return TJM_OK;
+}
+
+tjm_status tjm_selftest_tc_cgemm(int M, int N, int K, int conj_a, int conj_b, int a_col_major, int b_k_contig,
+                                 const double* A, const double* B, double* C) {
+  if (M < 1 || N < 1 || K < 1 || M > 1024 || N > 1024 || K > 1024 || !A || !B || !C) return TJM_EINVAL;
+  Dev d;
+  auto* dA = d.get<tjm::cx<double>>((size_t)M * K);
+  auto* dB = d.get<tjm::cx<double>>((size_t)K * N);
+  auto* dC = d.get<tjm::cx<double>>((size_t)M * N);
+  auto* fa = d.get<tjm::cx<float>>((size_t)M * K);
+  auto* fb = d.get<tjm::cx<float>>((size_t)K * N);
+  auto* fc = d.get<tjm::cx<float>>((size_t)M * N);
+  int* ok = d.get<int>(1);
+  if (!dA || !dB || !dC || !fa || !fb || !fc || !ok) return TJM_ENOMEM;
+  if (cudaMemcpy(dA, A, (size_t)M * K * 16, cudaMemcpyHostToDevice) != cudaSuccess) return TJM_ECUDA;
+  if (cudaMemcpy(dB, B, (size_t)K * N * 16, cudaMemcpyHostToDevice) != cudaSuccess) return TJM_ECUDA;
+  const int smem = tjm::tc::kSmemBytes + 1024;
+  if (cudaFuncSetAttribute(tjm::tc_cgemm_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return TJM_ECUDA;
+  tjm::tc_cgemm_test_kernel<<<1, TJM_THREADS, smem>>>(M, N, K, conj_a, conj_b, a_col_major, b_k_contig, dA, dB, dC,
+                                                     fa, fb, fc, ok);
+  if (finish()) return TJM_ECUDA;
+  int h = 0;
+  cudaMemcpy(&h, ok, sizeof h, cudaMemcpyDeviceToHost);
+  cudaMemcpy(C, dC, (size_t)M * N * 16, cudaMemcpyDeviceToHost);
+  return h ? TJM_OK : TJM_ETIMEOUT;
 }
 
 tjm_status tjm_selftest_expm_tridiag(int k, const double* alpha, const double* beta, double theta, double* c) {

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtjm.so")
 
 TJM_OK, TJM_EINVAL, TJM_ENOMEM, TJM_ENUMERIC, TJM_ETIMEOUT, TJM_EBUSY, TJM_EINTERNAL, TJM_ECUDA = range(8)
-PREC_FP64, PREC_FP32, PREC_FP32_DEC32 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_FP32_DEC32, PREC_FP32_DF64 = 0, 1, 2, 3
 STATE_ZERO, STATE_PRODUCT, STATE_PRODUCT_PER_TRAJ, STATE_MPS = 0, 1, 2, 3
 STATUS_NAMES = {0: "TJM_OK", 1: "TJM_EINVAL", 2: "TJM_ENOMEM", 3: "TJM_ENUMERIC", 4: "TJM_ETIMEOUT",
                 5: "TJM_EBUSY", 6: "TJM_EINTERNAL", 7: "TJM_ECUDA"}
@@ -95,6 +95,8 @@ SIGNATURES = [
                                   C.POINTER(C.c_double)]),
     ("tjm_selftest_svd", C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("tjm_selftest_tc_cgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("tjm_selftest_expm_tridiag", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
                                             C.POINTER(C.c_double)]),
     ("tjm_selftest_philox", C.c_int, [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
@@ -147,7 +149,7 @@ def _cplx(a):
 class Context:
     """One TJM problem (tjm_create) and the runs started on it."""
 
-    def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32, krylov_max=30, krylov_tol=0.0,
+    def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32_DF64, krylov_max=30, krylov_tol=0.0,
                  exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0):
         lib = load()
         self.lib = lib
@@ -338,7 +340,8 @@ def _z(a):
 
 
 def selftest_qr(A, double_precision=True):
-    """QR of one matrix by the kernel's block routine: returns (Q, R)."""
+    """QR of one matrix by the kernel's block routine: returns (Q, R).
+    double_precision: False/0 FP32, True/1 FP64, 2 double-float emulated FP64."""
     lib = load()
     A = np.asarray(A, dtype=np.complex128)
     m, n = A.shape
@@ -353,7 +356,8 @@ def selftest_qr(A, double_precision=True):
 
 
 def selftest_svd(A, double_precision=True):
-    """SVD of one matrix by the kernel's block routine: returns (U, S, V) with A = U diag(S) V^H."""
+    """SVD of one matrix by the kernel's block routine: returns (U, S, V) with A = U diag(S) V^H.
+    double_precision: False/0 FP32, True/1 FP64, 2 double-float emulated FP64."""
     lib = load()
     A = np.asarray(A, dtype=np.complex128)
     m, n = A.shape
@@ -366,6 +370,21 @@ def selftest_svd(A, double_precision=True):
     if st != TJM_OK:
         raise TJMError(st, "tjm_selftest_svd")
     return _z(U), S, _z(V)
+
+
+def selftest_tc_cgemm(A, B, conj_a=False, conj_b=False, a_col_major=False, b_k_contig=False):
+    """op(A) op(B) by the tensor-core complex GEMM (3xTF32, FP32 accumulation) on one CTA."""
+    lib = load()
+    A = np.asarray(A, dtype=np.complex128)
+    B = np.asarray(B, dtype=np.complex128)
+    M, K = A.shape
+    N = B.shape[1]
+    out = np.zeros((M, N, 2))
+    st = lib.tjm_selftest_tc_cgemm(M, N, K, int(conj_a), int(conj_b), int(a_col_major), int(b_k_contig),
+                                   _dp(_cplx(A)), _dp(_cplx(B)), _dp(out))
+    if st != TJM_OK:
+        raise TJMError(st, "tjm_selftest_tc_cgemm")
+    return _z(out)
 
 
 def selftest_expm_tridiag(alpha, beta, theta):

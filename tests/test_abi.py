@@ -42,7 +42,7 @@ def test_default_options(lib):
     o = tjm.tjm_options()
     lib.tjm_default_options(C.byref(o))
     assert (o.precision, o.krylov_max, o.krylov_tol, o.exact_full_bond, o.device, o.max_ctas) == \
-           (tjm.PREC_FP32, 30, 0.0, 0, 0, 0)
+           (tjm.PREC_FP32_DF64, 30, 0.0, 0, 0, 0)
     assert (o.energy_shift, o.tile_rule) == (1, 0)
 
 

@@ -2,7 +2,9 @@
 
 QR and SVD are checked through what defines them (orthonormal factors,
 reconstruction, triangularity, singular values equal to LAPACK's), so the
-gauge freedom of the factors does not matter.
+gauge freedom of the factors does not matter.  Each runs in the three
+factorization precisions: FP32 (dp=0), FP64 (dp=1) and double-float emulated
+FP64 (dp=2), whose 48-bit significand must give FP64-class results.
 """
 import numpy as np
 import pytest
@@ -38,10 +40,13 @@ def _cases():
     return out
 
 
-@pytest.mark.parametrize("dp", [1, 0])
+TOL = {0: 5e-5, 1: 1e-12, 2: 1e-11}
+
+
+@pytest.mark.parametrize("dp", [1, 0, 2])
 def test_qr_block(dp):
     lib_ready()
-    tol = 1e-12 if dp else 5e-5
+    tol = TOL[dp]
     for name, A in _cases():
         Q, R = tjm.selftest_qr(A, dp)
         k = min(A.shape)
@@ -51,10 +56,10 @@ def test_qr_block(dp):
         assert np.abs(np.tril(R, -1)).max() == 0.0, name
 
 
-@pytest.mark.parametrize("dp", [1, 0])
+@pytest.mark.parametrize("dp", [1, 0, 2])
 def test_svd_block(dp):
     lib_ready()
-    tol = 1e-12 if dp else 5e-5
+    tol = TOL[dp]
     for name, A in _cases():
         U, S, V = tjm.selftest_svd(A, dp)
         nn = min(A.shape)
@@ -104,10 +109,10 @@ def test_svd_rank_deficient_after_projection():
         Qb, _ = np.linalg.qr(_rand(rng, n, n))
         s = np.sort(rng.uniform(0.01, 1.0, r))[::-1]
         A = (Qa[:, :r] * s) @ Qb[:, :r].conj().T          # exact rank r, noise in the null space
-        for dp in (1, 0):
+        for dp in (1, 0, 2):
             U, S, V = tjm.selftest_svd(A, dp)
             nn = min(m, n)
-            tol = 1e-12 if dp else 5e-5
+            tol = TOL[dp]
             assert np.abs(U.conj().T @ U - np.eye(nn)).max() < 100 * tol, (m, n, r, dp)
             assert np.abs(V.conj().T @ V - np.eye(nn)).max() < 100 * tol, (m, n, r, dp)
             assert np.abs((U * S) @ V.conj().T - A).max() < 100 * tol, (m, n, r, dp)
@@ -122,10 +127,28 @@ def test_qr_rank_deficient_noise_columns():
         Qa, _ = np.linalg.qr(_rand(rng, m, m))
         Qb, _ = np.linalg.qr(_rand(rng, n, n))
         A = (Qa[:, :r] * rng.uniform(0.1, 1.0, r)) @ Qb[:, :r].conj().T
-        for dp in (1, 0):
+        for dp in (1, 0, 2):
             Q, R = tjm.selftest_qr(A, dp)
-            tol = 1e-12 if dp else 5e-5
+            tol = TOL[dp]
             k = min(m, n)
             assert np.isfinite(Q).all() and np.isfinite(R).all()
             assert np.abs(Q.conj().T @ Q - np.eye(k)).max() < 100 * tol, (m, n, r, dp)
             assert np.abs(Q @ R - A).max() < 100 * tol, (m, n, r, dp)
+
+
+def test_emulated_fp64_factorizations_equal_native_fp64():
+    """Double-float QR and SVD give the native FP64 results (singular values, the projector U U^H,
+    R up to the column phases of Q) to ~1e-13 on the factorization shapes of the sweeps."""
+    lib_ready()
+    rng = np.random.default_rng(11)
+    for (m, n) in [(128, 64), (64, 128), (128, 128), (32, 16)]:
+        A = _rand(rng, m, n) / np.sqrt(n)
+        U1, S1, V1 = tjm.selftest_svd(A, 1)
+        U2, S2, V2 = tjm.selftest_svd(A, 2)
+        assert np.abs(S1 - S2).max() < 1e-13 * S1[0], (m, n)
+        r = min(m, n) // 2
+        assert np.abs(U1[:, :r] @ U1[:, :r].conj().T - U2[:, :r] @ U2[:, :r].conj().T).max() < 1e-12, (m, n)
+        Q1, R1 = tjm.selftest_qr(A, 1)
+        Q2, R2 = tjm.selftest_qr(A, 2)
+        assert np.abs(np.abs(R1) - np.abs(R2)).max() < 1e-13 * np.abs(R1).max(), (m, n)
+        assert np.abs(Q1 @ R1 - Q2 @ R2).max() < 1e-13, (m, n)

@@ -75,7 +75,7 @@ def test_small_chain_fp64_all_trajectories_and_lindblad():
     assert np.allclose(sem, pt.std(axis=0, ddof=1) / np.sqrt(wl.n_traj), atol=1e-14)
 
 
-@pytest.mark.parametrize("prec", [tjm.PREC_FP32, tjm.PREC_FP32_DEC32])
+@pytest.mark.parametrize("prec", [tjm.PREC_FP32, tjm.PREC_FP32_DF64, tjm.PREC_FP32_DEC32])
 def test_small_chain_fp32_paths(prec):
     """L=6, 64 trajectories, FP32 contractions: per trajectory within 1e-4 of the FP64 oracle for the
     first 30 of 50 steps (rounding differences grow along a trajectory; the margins counted are those
