@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "trajectory*site*steps/s at L=1000 chi=64"
 UNIT = "trajectory*site*steps/s"
+# --precision value -> (library precision code, dtype of the JSON line)
+PRECISIONS = {"f32+df64": (3, "f32+df64"), "f32+f64": (1, "f32+f64"), "f32": (2, "f32"), "f64": (0, "f64")}
 
 
 def parse():
@@ -36,11 +38,16 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32d64", "fp64"])
+    p.add_argument("--precision", default="f32+df64", choices=list(PRECISIONS),
+                   help="f32+df64: FP32 contractions, QR/SVD in emulated FP64 (double-float); f32+f64: the same "
+                        "with native FP64 QR/SVD; f32: QR/SVD in FP32 too; f64: everything FP64")
     p.add_argument("--L", type=int, default=1000)
     p.add_argument("--chi", type=int, default=64)
     p.add_argument("--ntraj", type=int, default=256)
-    p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 slice")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 GPU arm")
+    p.add_argument("--fp64-traj", type=int, default=0,
+                   help="trajectories of the plain-FP64 GPU arm (0: one per SM; see DESIGN, FP64 is pipe-bound)")
+    p.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end tjm_run measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--ref-sites", type=int, default=200,
@@ -131,23 +138,27 @@ def _oracle_step_job(args):
     return time.perf_counter() - t0
 
 
-def oracle_sample(cores, L=24, chi=64, rounds=1):
-    """Time the oracle on `cores` trajectories at once (one per core), `rounds` steps each."""
+def oracle_rate(pool, cores, L, chi, first, seed):
+    """One timed oracle step: `cores` trajectories (one per core, in parallel) on an L-site slice.
+    Returns (wall seconds of the step, busy CPU seconds)."""
+    t0 = time.perf_counter()
+    per = pool.map(_oracle_step_job, [(L, chi, first + t, seed) for t in range(cores)])
+    return time.perf_counter() - t0, sum(per)
+
+
+def oracle_sample(cores, L, chi):
+    """The CPU baseline: the oracle as it stands on one step of `cores` trajectories of an L-site slice of
+    the benchmark's chi-saturated family, one trajectory per host core; rate from the wall time."""
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     import multiprocessing as mp
-    jobs = [(L, chi, t, 11) for t in range(cores * rounds)]
-    t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(cores) as pool:
-        per = pool.map(_oracle_step_job, jobs)
-    wall = time.perf_counter() - t0
-    busy = sum(per)
-    # throughput of the busy cores: trajectory*site*steps per second of wall time
-    value = len(jobs) * L / (busy / cores)
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d trajectories x 1 TJM step of an L=%d XXX chain at chi=%d (random chi-saturated MPS, "
-                      "same H, noise, dt), numpy FP64 oracle, one trajectory per core; per-site rate" %
-                      (len(jobs), L, chi),
+        pool.map(_oracle_step_job, [(8, chi, t, 11) for t in range(cores)])      # start-up of the workers
+        wall, busy = oracle_rate(pool, cores, L, chi, 0, 2025)
+    return {"value": cores * L / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d trajectories (one per core) x 1 TJM step of an L=%d slice of the chi=%d random "
+                      "chi-saturated family (seed 2025, same H, noise, dt), numpy FP64 oracle; per-site rate from "
+                      "the wall time of the step" % (cores, L, chi),
             "wall_s": wall, "cpu_s": busy}
 
 
@@ -155,7 +166,7 @@ def workload_config(a, world, state_bytes_per_elem):
     L, chi, N = a.L, a.chi, a.ntraj
     return {"workload": "xxx_L%d_chi%d_N%d_random_chi_saturated" % (L, chi, N), "L": L, "chi_max": chi,
             "trajectories_per_gpu": N, "dt": 0.1, "gamma": 0.1, "g": 0.5,
-            "precision": a.precision, "l2": "inputs larger than L2 (trajectory state %.1f GB)" %
+            "l2": "inputs larger than L2 (trajectory state %.1f GB)" %
             (N * (L * 2 * chi * chi + 2 * (L + 1) * 5 * chi * chi) * state_bytes_per_elem / 1e9),
             "parallelism": "trajectories" + ("x%d" % world if world > 1 else "")}
 
@@ -165,9 +176,10 @@ def run_reference(a):
 
     Each timed step is one oracle TJM step of `cores` trajectories (one per host core, in parallel)
     on a --ref-sites chain of the same random chi-saturated family (the bench's seed, same H, noise
-    and dt), reported per site: a full L=1000 oracle step takes ~100 s per core, so the slice keeps
-    the run to a few minutes; its ~5 % of edge sites with chi < 64 make the per-site rate slightly
-    optimistic for the CPU.  The warm-up steps run the same code on a 24-site chain.
+    and dt), reported per site from the measured wall time of the step: a full L=1000 oracle step
+    takes ~100 s per core, so the slice keeps the run to a few minutes; its ~5 % of edge sites with
+    chi < 64 make the per-site rate slightly optimistic for the CPU.  The warm-up steps run the same
+    code on an 8-site chain.
     """
     cores = max(1, min(os.cpu_count() or 1, 16))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,24 +190,57 @@ def run_reference(a):
     import multiprocessing as mp
     Ls = min(a.L, a.ref_sites)
     t0 = time.perf_counter()
+    walls = []
     with mp.get_context("spawn").Pool(cores) as pool:
         for _ in range(a.warmup):
-            pool.map(_oracle_step_job, [(24, a.chi, t, 11) for t in range(cores)])
-        busy = 0.0
+            pool.map(_oracle_step_job, [(8, a.chi, t, 11) for t in range(cores)])
         for k in range(a.steps):
-            per = pool.map(_oracle_step_job, [(Ls, a.chi, k * cores + t, 2025) for t in range(cores)])
-            busy += sum(per) / cores
-    value = a.steps * cores * Ls / busy
-    ms = 1000.0 * busy / a.steps * a.L / Ls        # per step of one L-site trajectory per core
+            walls.append(oracle_rate(pool, cores, Ls, a.chi, k * cores, 2025)[0])
+    wall = sum(walls)
+    value = a.steps * cores * Ls / wall
     sample = ("%d trajectories (one per core) x 1 oracle TJM step per timed step, on an L=%d slice of the "
-              "chi=%d random chi-saturated family (seed 2025), numpy FP64; per-site rate" % (cores, Ls, a.chi))
+              "chi=%d random chi-saturated family (seed 2025), numpy FP64; per-site rate from the wall time"
+              % (cores, Ls, a.chi))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference", "config": workload_config(a, 1, 16 if a.precision == "fp64" else 8),
+           "ms_per_step": 1000.0 * wall / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference", "config": workload_config(a, 1, 8),
+           "step": "one oracle TJM step of %d trajectories on the L=%d slice (measured)" % (cores, Ls),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": time.perf_counter() - t0}
     print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def csrc_digest():
+    """Digest of the CUDA sources: identifies the kernel version a profile was taken of."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2501_17913_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file, units_per_launch):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu summary, scaled to this launch's
+    units; None unless the summary was taken of the current sources (its `csrc digest:` line matches)."""
+    p = os.path.join(ROOT, "profiles", kernel_file)
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None, "no profile"
+    import re
+    dg = re.search(r"csrc digest:\s*([0-9a-f]{16})", txt)
+    per = re.search(r"dram bytes per unit:\s*([0-9.eE+]+)", txt)
+    if not dg or not per:
+        return None, "profile lacks digest or per-unit bytes"
+    if dg.group(1) != csrc_digest():
+        return None, "kernel changed since the profile (%s)" % dg.group(1)
+    return float(per.group(1)) * units_per_launch, "profiles/%s scaled by units" % kernel_file
 
 
 # ----------------------------------------------------------------------------- ours (GPU)
@@ -221,7 +266,7 @@ def main():
         B.build()
     if dist:
         dist.barrier()
-    prec = {"fp32": tjm.PREC_FP32_DEC32, "fp32d64": tjm.PREC_FP32, "fp64": tjm.PREC_FP64}[a.precision]
+    prec, dtype = PRECISIONS[a.precision]
     L, chi, N, dt = a.L, a.chi, a.ntraj, 0.1
     n_total = a.warmup + a.steps
     W = I.xxx_mpo(L, 1.0, 0.5)
@@ -264,53 +309,69 @@ def main():
     value, t_max = job_rate(N * L * a.steps, ms)       # all ranks' units over the slowest rank's time
     fc = s1["flops_contract"] - s0["flops_contract"]
     fd = s1["flops_decomp"] - s0["flops_decomp"]
+    cyc = {k: s1["cycles"][k] - s0["cycles"][k] for k in s1["cycles"]}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # CUDA-core FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
-    fp64_peak = n_sm * 2 * 2 * sm_max * 1e6 / 1e12      # FP64 FMA: 2 per SM per clock on GB300
     achieved = fc / (ms / 1000.0) / 1e12
-    if prec == tjm.PREC_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None}
+    # The contractions' roofline is the tensor pipe.  TF32 (the FP32-input tensor format) runs at half the
+    # BF16 rate; the denominator is the measured sustained cuBLAS BF16 rate (a kernel timed inside a long
+    # step) halved, else the recipe's fallback.
+    if "bf16_tflops_sustained" in peaks:
+        bf16, src = float(peaks["bf16_tflops_sustained"]), "measured"
     else:
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None}
+        bf16, src = 1700.0, "fallback"
+    fp32_core = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    fp64_core = n_sm * 2 * 2 * sm_max * 1e6 / 1e12       # FP64 FMA: 2 per SM per clock on GB300
+    if prec == tjm.PREC_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_core, "unit": "TFLOP/s",
+                "frac": achieved / fp64_core,
+                "peak_source": "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, sm_max)}
+    else:
+        tf32 = bf16 / 2.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32, "unit": "TFLOP/s", "frac": achieved / tf32,
+                "peak_source": "TF32 = %s sustained BF16 %.1f TFLOP/s / 2 (of %s)" % (src, bf16, src),
+                "cuda_core_fp32": {"peak": fp32_core, "frac": achieved / fp32_core,
+                                   "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz"
+                                                  % (n_sm, sm_max)}}
     roof["kernel"] = "tjm::advance_kernel"
-    roof["peak_source"] = "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (CUDA-core FMA)" % (n_sm, sm_max) \
-        if prec != tjm.PREC_FP64 else "derived: %d SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz" % (n_sm, sm_max)
-    roof["achieved_counts"] = "contraction flops counted on device (8 per complex MAC) / CUDA-event time"
+    roof["achieved_counts"] = "contraction flops counted on device (8 per complex MAC) / CUDA-event time of the launches"
+    traffic, tsrc = profiled_traffic("advance_kernel_traffic_bench.md", N * L)
+    roof["traffic"] = traffic
+    roof["traffic_source"] = tsrc
     roof["decomp_tflops"] = fd / (ms / 1000.0) / 1e12
+    tot_cyc = max(1, sum(v for k, v in cyc.items() if k in ("tdvp", "dissipate_jump", "env_build", "measure")))
+    roof["phase_share"] = {k: cyc[k] / tot_cyc for k in ("gemm", "mpo_contract", "lanczos", "qr", "svd", "matvec",
+                                                         "krylov_expm", "tdvp", "dissipate_jump", "env_build",
+                                                         "measure")}
     extra = {}
     # end to end through the C ABI with host buffers: tjm_run (init + F_0 + K steps) and tjm_result
     if not a.no_e2e:
+        ke = max(1, min(a.steps, a.e2e_steps))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local, tile_rule=rule)
-        times2 = [dt * j for j in range(a.steps + 1)]
+        times2 = [dt * j for j in range(ke + 1)]
         r2 = ctx2.run(psi, N, 0, obs, times2, first_traj=rank * N)
         mean, sem, pt = ctx2.result(r2)
         t_e2e = time.perf_counter() - t0
         h2d = sum(x.size for x in psi[1]) * 16 + len(psi[0]) * 4
         d2h = pt.nbytes + mean.nbytes + sem.nbytes
-        e2e = {"value": world * N * L * a.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // a.steps,
-               "d2h_bytes_per_step": d2h // a.steps, "wall_s": t_e2e,
-               "note": "tjm_run from host inputs (init, F_0, K steps) + tjm_result to host"}
-        gpu_launches_e2e = ctx2.launches()
+        e2e = {"value": world * N * L * ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // ke,
+               "d2h_bytes_per_step": d2h // ke, "wall_s": t_e2e, "steps": ke,
+               "note": "tjm_run from host inputs (upload, init, F_0, %d steps) + tjm_result to host" % ke}
         ctx2.close()
     else:
         e2e = None
-    # plain FP64 GPU path on a slice of the workload (same H, noise, dt, chi; L=100, 1 step)
+    # plain FP64 GPU path on the same workload (L, chi, H, noise, dt, random chi-saturated start): one timed step
     if not a.no_fp64 and rank == 0:
-        L64, N64 = 100, n_sm
-        W64 = I.xxx_mpo(L64, 1.0, 0.5)
-        ctx3 = tjm.Context(W64, I.noise(L64, 0.1, 0.1), dt, chi, 1e-10, precision=tjm.PREC_FP64, device=local)
-        r3 = ctx3.prepare(I.random_mps(L64, chi, 2025), N64, 0, I.z_observables(L64), [dt, 2 * dt])
+        N64 = a.fp64_traj or n_sm
+        ctx3 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=tjm.PREC_FP64, device=local)
+        r3 = ctx3.prepare(psi, N64, 0, obs, [dt, 2 * dt])
         ctx3.advance(r3, 0)
         ctx3.sync()
         st3 = torch.cuda.ExternalStream(ctx3.stream())
@@ -321,19 +382,23 @@ def main():
         f1.record(st3)
         f1.synchronize()
         ms64 = f0.elapsed_time(f1)
-        extra["fp64_gpu"] = {"value": N64 * L64 / (ms64 / 1000.0), "unit": UNIT,
-                             "slice": "%d trajectories x 1 step, L=%d, chi=64 (random chi-saturated MPS)" % (N64, L64),
+        extra["fp64_gpu"] = {"value": N64 * L / (ms64 / 1000.0), "unit": UNIT, "same_config": True,
+                             "slice": "%d trajectories x 1 timed step, L=%d, chi=%d (random chi-saturated MPS, the "
+                                      "bench's seed), FP64 contractions and factorizations" % (N64, L, chi),
                              "ms": ms64}
         ctx3.close()
     cpu = None
     if not a.no_cpu and rank == 0:
-        cpu = oracle_sample(max(1, min(os.cpu_count() or 1, 16)))
+        cpu = oracle_sample(max(1, min(os.cpu_count() or 1, 16)), min(L, a.ref_sites), chi)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None,
-               "dtype": {"fp32": "f32", "fp32d64": "f32+f64", "fp64": "f64"}[a.precision],
-               "data": "synthetic",
+               "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+               "arithmetic": {"f32+df64": "FP32 contractions (FP32 accumulation); QR/SVD in double-float emulated "
+                                          "FP64; norms, jump weights, Lanczos coefficients in FP64",
+                              "f32+f64": "FP32 contractions; QR/SVD in native FP64; FP64 reductions",
+                              "f32": "FP32 contractions and QR/SVD; FP64 reductions",
+                              "f64": "FP64 throughout"}[a.precision],
                "config": workload_config(a, world, 8 if prec else 16),
                "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
                "tile_autotune": {"rule": rule, "trials": tuner.report()},
