@@ -90,6 +90,15 @@ typedef struct {
   double op[8];
 } tjm_observable;
 
+/* A two-site observable O on (site, site + 1), e.g. the nearest-neighbour
+ * correlator X (x) X of Fig. 4b: 4 x 4 complex, row-major, row index
+ * (t1 t2) and column index (s1 s2) with `site` the more significant.  The
+ * library returns Re <Psi|O|Psi> per trajectory. */
+typedef struct {
+  int site;
+  double op[32];
+} tjm_observable2;
+
 /* Initial state Psi(0) (Sec. "Initialization" item 1). */
 enum { TJM_STATE_ZERO = 0, TJM_STATE_PRODUCT = 1, TJM_STATE_PRODUCT_PER_TRAJ = 2, TJM_STATE_MPS = 3 };
 typedef struct {
@@ -114,6 +123,13 @@ typedef struct {
                          * so observables are unchanged; it keeps the FP32 environment sums near
                          * zero instead of near the extensive energy.  0: evolve with H as given. */
   int tile_rule;        /* initial GEMM tile rule of new runs (see tjm_run_set_tile_rule); default 0 */
+  int tensor_cores;     /* 1 (default): FP32 contractions of at least 16384 complex multiply-adds run on the
+                         * tensor cores (tcgen05, TF32 inputs split hi + lo, "3xTF32", FP32 accumulation);
+                         * 0: on the CUDA cores in FP32.  FP64 contractions always use the CUDA cores. */
+  int trotter_order;    /* 2 (default): the Strang-split TJM with its sampling layer (Sec. "Higher-order
+                         * Trotterization", Eq. SimulationStep).  1: the first-order baseline the paper
+                         * compares with (Fig. 4a, dotted): Phi_j = J(D[dt] U[dt] Phi_{j-1}) from
+                         * Phi_0 = Psi(0), and Psi(j dt) = Phi_j is measured directly. */
 } tjm_options;
 
 /* Fill opts with the defaults above. */
@@ -146,6 +162,17 @@ tjm_status tjm_run(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t 
  * the run so that tjm_run_advance can move it forward step by step. */
 tjm_status tjm_run_prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
                            const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id);
+
+/* tjm_run_prepare2 / tjm_run2 -- as tjm_run_prepare / tjm_run with two-site
+ * observables as well: every output row holds the n_obs one-site values
+ * followed by the n_obs2 two-site values (results then have n_obs + n_obs2
+ * columns in tjm_result).  A two-site observable needs site + 1 < L. */
+tjm_status tjm_run_prepare2(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                            const tjm_observable* obs, int n_obs, const tjm_observable2* obs2, int n_obs2,
+                            const double* times, int n_times, int64_t* run_id);
+tjm_status tjm_run2(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                    const tjm_observable* obs, int n_obs, const tjm_observable2* obs2, int n_obs2, const double* times,
+                    int n_times, int64_t* run_id);
 
 /* tjm_run_advance -- launch one persistent kernel that moves every trajectory
  * of the run forward by at most max_steps time steps (the first call also
@@ -280,6 +307,23 @@ tjm_status tjm_selftest_svd(int double_precision, int m, int n, const double* A,
  * TJM_ETIMEOUT if the kernel's bounded wait for the tensor cores ran out. */
 tjm_status tjm_selftest_tc_cgemm(int M, int N, int K, int conj_a, int conj_b, int a_col_major, int b_k_contig,
                                  const double* A, const double* B, double* C);
+
+/* One effective-Hamiltonian application or environment update of the
+ * trajectory kernel (Fig. 2 networks; environment recursion of Sec. "Hybrid
+ * strategy"), by the same device functions the sweeps call, on one CTA.
+ * Layouts (complex doubles, row-major): Lenv [chl][Dl][chl] (bra, MPO, ket),
+ * Renv [Dr][chr][chr] (MPO, ket, bra), W1 [Dl][Dr or Du][2][2] and W2
+ * [Du][Dr][2][2] (MPO left, right, out, in).
+ *   kind 0  bond:      y[chl][chr]       = sum Lenv[x,w,a] x[a,b] Renv'[w,b,y]  (Renv' is [Dl][chr][chr])
+ *   kind 1  one site:  y[chl][2][chr]    = sum Lenv W1 x Renv
+ *   kind 2  two sites: y[chl][2][2][chr] = sum Lenv W1 W2 x Renv
+ *   kind 3  left env:  y[chr][Dr][chr]   = sum conj(x) Lenv W1 x      (x = A [chl][2][chr])
+ *   kind 4  right env: y[Dl][chl][chl]   = sum x W1 Renv conj(x)      (x = B [chl][2][chr])
+ * precision TJM_PREC_FP64 or TJM_PREC_FP32 (FP32 contractions; tensor_cores
+ * selects tcgen05 or the CUDA cores).  chl, chr <= 64; D <= 8. */
+tjm_status tjm_selftest_contract(int kind, int precision, int tensor_cores, int chl, int chr, int Dl, int Du, int Dr,
+                                 const double* W1, const double* W2, const double* Lenv, const double* Renv,
+                                 const double* x, double* y);
 
 /* exp(i theta T) e_1 for the k x k (k <= 32) real symmetric tridiagonal
  * T = tridiag(beta, alpha, beta): the Lanczos exponential's small factor

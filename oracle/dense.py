@@ -41,6 +41,14 @@ def site_operator(op, site, L, d=2):
     return out
 
 
+def _operator(op, site, L, d=2):
+    """A one-site (d x d) or nearest-neighbour two-site (d^2 x d^2, on site, site + 1) operator, dense."""
+    op = np.asarray(op, dtype=np.complex128)
+    if op.shape == (d, d):
+        return site_operator(op, site, L, d)
+    return np.kron(np.kron(np.eye(d ** site), op), np.eye(d ** (L - site - 2)))
+
+
 def apply_site(op, psi, site, L, d=2):
     """Apply a d x d operator to one site of a dense state vector."""
     t = psi.reshape([d] * L)
@@ -106,10 +114,12 @@ class DenseStrang:
         psi = math.sqrt(g) * apply_site(op, psi, s, self.L, self.d)
         return psi / np.linalg.norm(psi), rec
 
-    def run(self, psi0, traj_id, seed, observables, n_steps, sample_steps):
+    def run(self, psi0, traj_id, seed, observables, n_steps, sample_steps, order=2):
+        """order 2: the TJM schedule; order 1: Psi(j dt) = J(D[dt] U Psi((j-1) dt)) measured directly,
+        the first-order baseline (same readings as O1's run_trajectory)."""
         psi = np.asarray(psi0, dtype=np.complex128)
         psi = psi / np.linalg.norm(psi)
-        obs = [site_operator(op, s, self.L, self.d) for (s, op) in observables]
+        obs = [_operator(op, s, self.L, self.d) for (s, op) in observables]
 
         def meas(p):
             return np.array([np.vdot(p, O @ p).real for O in obs]) / float(np.vdot(p, p).real)
@@ -118,6 +128,14 @@ class DenseStrang:
         vals, recs = {}, []
         if 0 in want:
             vals[0] = meas(psi)
+        if order == 1:
+            for j in range(1, n_steps + 1):
+                u1, u2 = uniforms(seed, traj_id, j, 0)
+                psi, r = self.dj(self.U @ psi, self.dt, u1, u2)
+                recs.append(r)
+                if j in want:
+                    vals[j] = meas(psi)
+            return np.array([vals[s] for s in sample_steps]), recs
         if n_steps > 0:
             u1, u2 = uniforms(seed, traj_id, 0, 0)
             psi, r = self.dj(psi, 0.5 * self.dt, u1, u2)
@@ -172,5 +190,35 @@ def lindblad_evolve(H, jumps, L, rho0, times, d=2, rtol=1e-12, atol=1e-13):
     return out
 
 
+def lindblad_steady_state(H, jumps, L, d=2):
+    """O3 steady state: the trace-one solution of L(rho) = 0 (Eq. Lindblad with d rho/dt = 0).
+
+    The Liouvillian is assembled as a sparse superoperator on row-major vec(rho)
+    (vec(A rho B) = (A kron B^T) vec(rho)); one of its rows is replaced by the
+    trace condition sum_i rho_ii = 1 and the linear system is solved directly.
+    Assumes a unique steady state (as for the boundary-driven chain).
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    H = np.asarray(H, dtype=np.complex128)
+    n = H.shape[0]
+    jd = [(site_operator(np.asarray(op, dtype=np.complex128), s, L, d), float(g)) for (s, op, g) in jumps]
+    LdL = sum(g * (Lm.conj().T @ Lm) for (Lm, g) in jd) if jd else np.zeros_like(H)
+    Heff = sp.csr_matrix(H - 0.5j * LdL)
+    Id = sp.identity(n, format='csr', dtype=np.complex128)
+    # d rho/dt = -i (Heff rho - rho Heff^dag) + sum_m g L rho L^dag
+    Lv = -1j * (sp.kron(Heff, Id) - sp.kron(Id, Heff.conj()))
+    for (Lm, g) in jd:
+        Ls = sp.csr_matrix(Lm)
+        Lv = Lv + g * sp.kron(Ls, Ls.conj())
+    A = Lv.tolil()
+    A[0, :] = 0
+    for i in range(n):
+        A[0, i * n + i] = 1.0
+    b = np.zeros(n * n, dtype=np.complex128)
+    b[0] = 1.0
+    return spl.spsolve(A.tocsc(), b).reshape(n, n)
+
+
 def expect(rho, op, site, L, d=2):
-    return float(np.trace(rho @ site_operator(op, site, L, d)).real)
+    return float(np.trace(rho @ _operator(op, site, L, d)).real)

@@ -133,10 +133,13 @@ def trunc_rank(S, prob: Problem, rec=None) -> int:
 
 
 def local_expectations(mps, ops):
-    """<psi|O_i|psi> for single-site operators [(site, op)], by the plain definition.
+    """<psi|O_i|psi> for local operators [(site, op)], by the plain definition.
 
-    Left and right transfer matrices are built once with no canonical-form
-    assumption; the values are NOT divided by <psi|psi>.  Also returns <psi|psi>.
+    op is 2 x 2 (acting on `site`) or 4 x 4 (acting on sites `site`, `site`+1,
+    row index (t1 t2), column index (s1 s2), the first site most significant;
+    the two-site correlators of Fig. 4b, e.g. X (x) X).  Left and right transfer
+    matrices are built once with no canonical-form assumption; the values are
+    NOT divided by <psi|psi>.  Also returns <psi|psi>.
     """
     L = len(mps)
     Lt = [np.ones((1, 1), dtype=np.complex128)]
@@ -149,8 +152,15 @@ def local_expectations(mps, ops):
     norm2 = Lt[L][0, 0].real
     vals = []
     for (site, op) in ops:
+        op = np.asarray(op)
         M = mps[site]
-        vals.append(np.einsum('ab,atc,ts,bsd,cd->', Lt[site], M.conj(), op, M, Rt[site + 1], optimize=True))
+        if op.shape == (2, 2):
+            vals.append(np.einsum('ab,atc,ts,bsd,cd->', Lt[site], M.conj(), op, M, Rt[site + 1], optimize=True))
+        else:
+            N = mps[site + 1]
+            O4 = op.reshape(2, 2, 2, 2)       # [t1, t2, s1, s2]
+            vals.append(np.einsum('ab,atc,cue,tusv,bsd,dvf,ef->', Lt[site], M.conj(), N.conj(), O4, M, N,
+                                  Rt[site + 2], optimize=True))
     return np.array(vals), norm2
 
 
@@ -480,7 +490,7 @@ def padded_product_mps(phis, rng=None):
 # --------------------------------------------------------------------------
 # one trajectory (Sec. "Algorithm": sampling MPS Phi, F_0, F_j, F_n)
 # --------------------------------------------------------------------------
-def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sample_steps):
+def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sample_steps, order=2):
     """Observables of one TJM trajectory at the sampled steps.
 
     Reading of the sampling-MPS indexing (Eqs. TimeEvolutionFunctions,
@@ -488,6 +498,9 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
     Phi_0 = J(D[dt/2] Psi(0)); for j = 1..n: X = U[dt] Phi_{j-1};
     Psi(j dt) = J'(D[dt/2] X) on a copy (own uniforms, branch 1);
     Phi_j = J(D[dt] X) if j < n (branch 0).
+    order=1 is the first-order baseline of Fig. 4a (dotted lines), read as the
+    plain Lie-Trotter product with the same U, D and J: for j = 1..n
+    Psi(j dt) = J(D[dt] U[dt] Psi((j-1) dt)) (branch 0), measured directly.
     Returns (values[n_sample, n_obs], stats).
     """
     mps = [np.array(m, dtype=np.complex128) for m in psi0]
@@ -511,10 +524,18 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
     sw = Sweeper(prob)
     if 0 in want:
         vals[0] = measure(mps, observables)
-    if n_steps > 0:
+    if order == 1:
+        for j in range(1, n_steps + 1):
+            sw.build_right_envs(mps)
+            sw.sweep(mps, 0.5 * prob.dt)
+            u1, u2 = uniforms(seed, traj_id, j, 0)
+            note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec), j)
+            if j in want:
+                vals[j] = measure(mps, observables)
+    if order == 2 and n_steps > 0:
         u1, u2 = uniforms(seed, traj_id, 0, 0)
         note(dissipate_and_jump(mps, prob, D_half, u1, u2, sw.rec), 0)
-    for j in range(1, n_steps + 1):
+    for j in range(1, n_steps + 1 if order == 2 else 1):
         sw.build_right_envs(mps)
         sw.sweep(mps, 0.5 * prob.dt)
         if j in want:

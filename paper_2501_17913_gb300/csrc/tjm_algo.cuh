@@ -40,7 +40,9 @@ template <class Tc, class Td> struct Ctx {
   cx<Tc>* E; cx<Tc>* F;
   cx<Td>* da; cx<Td>* du; cx<Td>* dv; cx<Td>* dvw; cx<Td>* drd; Td* dtau; Td* ds; int* iw;
   cx<double>* G;         // [L][4] per-site reduced 2x2 blocks
+  cx<double>* G2;        // [L][16] reduced 4x4 blocks of sites (l, l+1) where a two-site observable starts
   double* wts;           // jump weights
+  char* wcsr;            // row-sparse MPO block of a fused tensor-core matvec
   // shared memory
   char* gsm; double* red; double* sc;
   char* fsm;             // factorization workspace in shared memory (nullptr if none)
@@ -107,7 +109,7 @@ __device__ __noinline__ void heff1(const Ctx<Tc, Td>& c, int l, const cx<Tc>* x,
   if constexpr (sizeof(Tc) == 4) {
     // G2 + G3 fused: the MPO block is applied while G3 loads its A tiles
     TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, kD, Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, c.Renv(l + 1), y,
-                                        c.gsm, site_shift(c), kD, Dr - 1, Dr, 0, 1));
+                                        c.gsm, c.wcsr, site_shift(c), kD, Dr - 1, Dr, 0, 1));
   } else {
     // G2: T2[x][(t v)][b] = sum_(w s) Wm1[(t v)][(w s)] T1[x][(w s)][b]
     TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
@@ -128,7 +130,7 @@ __device__ __noinline__ void heff2(const Ctx<Tc, Td>& c, int l, int chl, int chr
   TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, d2 * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, d2 * chr, 1), c.t1, d2 * chr, 1, c.gsm));
   if constexpr (sizeof(Tc) == 4) {
     TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, d2, Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, c.Renv(l + 2), y,
-                                        c.gsm, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
+                                        c.gsm, c.wcsr, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
   } else {
     TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, d2 * Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, (long long)Dl * d2 * chr, chr, c.t2,
                    (long long)d2 * Dr * chr, chr, c.gsm, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
@@ -610,8 +612,12 @@ __device__ __noinline__ void tdvp_sweep(const Ctx<Tc, Td>& c, double tau) {
 // G[l][t][s] = sum conj(M_l[a',t,b]) E_l[a',a] M_l[a,s,b] with E_l the left
 // transfer matrix of sites 0..l-1 (E_0 = 1).  Then <psi|O_l|psi> =
 // sum_ts O[t][s] G[l][t][s] and <psi|psi> = G[l][0][0] + G[l][1][1].
+//
+// With two_site, also G2[l][(t1 t2)][(s1 s2)] = sum conj(Th[a',t1,t2,b]) (E_l Th)[a',s1,s2,b] for the
+// sites l flagged in site_has2, Th = M_l M_{l+1} (sites l+2.. are right-canonical), so that
+// <psi|O_{l,l+1}|psi> = sum O[(t1 t2)][(s1 s2)] G2[l][(t1 t2)][(s1 s2)].
 template <class Tc, class Td>
-__device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m) {
+__device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m, bool two_site = false) {
   const int L = c.P->L;
   if (threadIdx.x == 0) c.E[0] = mk((Tc)1, (Tc)0);
   __syncthreads();
@@ -638,6 +644,43 @@ __device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m
     blk_sums_finish(8, c.red, c.sc + 448);
     if (threadIdx.x == 0)
       for (int q = 0; q < 4; ++q) c.G[(long long)l * 4 + q] = mk(c.sc[448 + 2 * q], c.sc[448 + 2 * q + 1]);
+    if (two_site && l + 1 < L && c.P->site_has2[l]) {
+      const int chm = m.chi[l + 1], chn = m.chi[l + 2];
+      const cx<Tc>* N = m.site(l + 1);
+      // Th[(a s1), (s2 b)] = M_l[(a s1), c] M_{l+1}[c, (s2 b)];  T[a', (s1 s2 b)] = E[a', a] Th[a, (s1 s2 b)]
+      TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * kD, kD * chn, chm, matA(M, chm, 1), matB(N, kD * chn, 1), c.theta,
+                                         kD * chn, 1, c.gsm));
+      TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl, kD * kD * chn, chl, matA(c.E, chl, 1), matB(c.theta, kD * kD * chn, 1),
+                                         c.tmp, kD * kD * chn, 1, c.gsm));
+      cx<Tc> h[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) h[q] = czero<Tc>();
+      for (int e = threadIdx.x; e < chl * chn; e += TJM_THREADS) {
+        const int a = e / chn, b = e % chn;
+        cx<Tc> th[4], tt[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          th[p] = c.theta[((long long)a * 4 + p) * chn + b];
+          tt[p] = c.tmp[((long long)a * 4 + p) * chn + b];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfma_cj(h[p * 4 + q], th[p], tt[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const double hx = warp_sum((double)h[q].x), hy = warp_sum((double)h[q].y);
+        if ((threadIdx.x & 31) == 0) {
+          c.red[(2 * q) * TJM_WARPS + (threadIdx.x >> 5)] = hx;
+          c.red[(2 * q + 1) * TJM_WARPS + (threadIdx.x >> 5)] = hy;
+        }
+      }
+      blk_sums_finish(32, c.red, c.sc + 448);
+      if (threadIdx.x < 16)
+        c.G2[(long long)l * 16 + threadIdx.x] = mk(c.sc[448 + 2 * threadIdx.x], c.sc[448 + 2 * threadIdx.x + 1]);
+      __syncthreads();
+    }
     // E'[b'][b] = sum_(a' s) conj(M[a'][s][b']) F[a'][s][b]
     if (l + 1 < L)
       TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chr, chr, chl * kD, matA(M, 1, chr, 1), matB(c.F, chr, 1), c.E, chr, 1, c.gsm));
@@ -647,9 +690,9 @@ __device__ __noinline__ void local_blocks(const Ctx<Tc, Td>& c, const Mps<Tc>& m
 
 template <class Tc, class Td>
 __device__ void measure(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int row) {
-  local_blocks(c, m);
   const ProbDev* P = c.P;
-  double* out = c.S->out + (long long)row * P->n_obs;
+  local_blocks(c, m, P->n_obs2 > 0);
+  double* out = c.S->out + (long long)row * (P->n_obs + P->n_obs2);
   for (int o = threadIdx.x; o < P->n_obs; o += TJM_THREADS) {
     const int l = P->osite[o];
     const cx<double>* op = P->oop + 4 * o;
@@ -657,6 +700,15 @@ __device__ void measure(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int row) {
     cx<double> v = czero<double>();
     for (int q = 0; q < 4; ++q) cfma(v, op[q], g[q]);
     out[o] = v.x / (g[0].x + g[3].x);
+  }
+  for (int o = threadIdx.x; o < P->n_obs2; o += TJM_THREADS) {
+    const int l = P->osite2[o];
+    const cx<double>* op = P->oop2 + 16 * o;
+    const cx<double>* g2 = c.G2 + 16 * (long long)l;
+    const cx<double>* g = c.G + 4 * (long long)l;
+    cx<double> v = czero<double>();
+    for (int q = 0; q < 16; ++q) cfma(v, op[q], g2[q]);
+    out[P->n_obs + o] = v.x / (g[0].x + g[3].x);
   }
   __syncthreads();
 }

@@ -20,6 +20,7 @@
 #include "tjm.h"
 #include "tjm_kernels.cuh"
 #include "tjm_launch.h"
+#include "tjm_mpo_layout.h"
 
 using tjm::cx;
 typedef std::complex<double> zc;
@@ -266,6 +267,8 @@ void tjm_default_options(tjm_options* o) {
   o->max_ctas = 0;
   o->energy_shift = 1;
   o->tile_rule = 0;
+  o->tensor_cores = 1;
+  o->trotter_order = 2;
 }
 
 const char* tjm_last_error(const tjm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -283,6 +286,8 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   tjm_options& o = ctx->opt;
   if (o.precision < 0 || o.precision > 3) return fail(nullptr, TJM_EINVAL, "");
   if (o.tile_rule < 0 || o.tile_rule > 1) return fail(nullptr, TJM_EINVAL, "");
+  if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(nullptr, TJM_EINVAL, "");
+  if (o.trotter_order != 1 && o.trotter_order != 2) return fail(nullptr, TJM_EINVAL, "");
   if (o.krylov_max <= 0 || o.krylov_max > 30) o.krylov_max = 30;
   if (!(o.krylov_tol > 0)) o.krylov_tol = o.precision == TJM_PREC_FP64 ? 1e-12 : 1e-7;
   const int L = H->L;
@@ -346,31 +351,16 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   }
   if (!ctx->opt.energy_shift) ctx->shift_ok = 0;
   // kernel layouts of the MPO
-  for (int l = 0; l < L; ++l) {
-    const int Dl = ctx->Dbond[l], Dr = ctx->Dbond[l + 1];
-    ctx->Wm1_off.push_back((long long)ctx->Wm1.size());
-    const int O1 = d * Dr, I1 = Dl * d;
-    for (int o = 0; o < O1; ++o)
-      for (int i = 0; i < I1; ++i) ctx->Wm1.push_back(Wel(l, i / d, o % Dr, o / Dr, i % d));
-    ctx->WmR_off.push_back((long long)ctx->WmR.size());
-    const int OR = Dl * d, IR = d * Dr;
-    for (int o = 0; o < OR; ++o)
-      for (int i = 0; i < IR; ++i) ctx->WmR.push_back(Wel(l, o / d, i % Dr, o % d, i / Dr));
+  {
+    tjm_host::MpoLayouts lay;
+    tjm_host::mpo_layouts(ctx->Dbond, ctx->Wsite, d, lay);
+    ctx->Wm1 = std::move(lay.Wm1);
+    ctx->WmR = std::move(lay.WmR);
+    ctx->W12 = std::move(lay.W12);
+    ctx->Wm1_off = std::move(lay.Wm1_off);
+    ctx->WmR_off = std::move(lay.WmR_off);
+    ctx->W12_off = std::move(lay.W12_off);
   }
-  for (int l = 0; l + 1 < L; ++l) {
-    const int Dl = ctx->Dbond[l], Du = ctx->Dbond[l + 1], Dr = ctx->Dbond[l + 2];
-    ctx->W12_off.push_back((long long)ctx->W12.size());
-    const int O = d * d * Dr, I = Dl * d * d;
-    for (int o = 0; o < O; ++o)
-      for (int i = 0; i < I; ++i) {
-        const int t1 = (o / Dr) / d, t2 = (o / Dr) % d, v = o % Dr;
-        const int w = i / (d * d), s1 = (i % (d * d)) / d, s2 = i % d;
-        zc acc = 0.0;
-        for (int u = 0; u < Du; ++u) acc += Wel(l, w, u, t1, s1) * Wel(l + 1, u, v, t2, s2);
-        ctx->W12.push_back(acc);
-      }
-  }
-  ctx->W12_off.push_back((long long)ctx->W12.size());
   // jumps, site-major (stable in the caller's order), and the dissipators
   std::vector<int> idx(n_jumps);
   for (int m = 0; m < n_jumps; ++m) {
@@ -433,11 +423,13 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
 }
 
 static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
-                          const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id) {
+                          const tjm_observable* obs, int n_obs1, const tjm_observable2* obs2, int n_obs2,
+                          const double* times, int n_times, int64_t* run_id) {
   if (!ctx) return TJM_EINVAL;
-  if (!run_id || n_traj < 1 || n_traj > (1LL << 30) || first_traj < 0 || n_obs < 0 || (n_obs && !obs) ||
-      n_times < 1 || !times)
+  if (!run_id || n_traj < 1 || n_traj > (1LL << 30) || first_traj < 0 || n_obs1 < 0 || (n_obs1 && !obs) ||
+      n_obs2 < 0 || (n_obs2 && !obs2) || n_times < 1 || !times)
     return fail(ctx, TJM_EINVAL, "bad run arguments");
+  const int n_obs = n_obs1 + n_obs2;     // output columns: one-site observables, then two-site ones
   TJM_CU(cudaSetDevice(ctx->device));
   const int L = ctx->L;
   const double dt = ctx->dt;
@@ -460,9 +452,17 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   R.n_steps = steps.back();
   std::vector<int> sample_row(R.n_steps + 1, -1);
   for (int i = 0; i < n_times; ++i) sample_row[steps[i]] = i;
-  std::vector<int> osite(n_obs);
-  std::vector<zc> oop((size_t)n_obs * 4);
-  for (int o = 0; o < n_obs; ++o) {
+  std::vector<int> osite(n_obs1);
+  std::vector<zc> oop((size_t)n_obs1 * 4);
+  std::vector<int> osite2(n_obs2), has2(L, 0);
+  std::vector<zc> oop2((size_t)n_obs2 * 16);
+  for (int o = 0; o < n_obs2; ++o) {
+    if (obs2[o].site < 0 || obs2[o].site + 1 >= L) return fail(ctx, TJM_EINVAL, "two-site observable out of range");
+    osite2[o] = obs2[o].site;
+    has2[obs2[o].site] = 1;
+    for (int q = 0; q < 16; ++q) oop2[(size_t)o * 16 + q] = cplx(obs2[o].op + 2 * q);
+  }
+  for (int o = 0; o < n_obs1; ++o) {
     if (obs[o].site < 0 || obs[o].site >= L) return fail(ctx, TJM_EINVAL, "observable site out of range");
     osite[o] = obs[o].site;
     for (int q = 0; q < 4; ++q) oop[(size_t)o * 4 + q] = cplx(obs[o].op + 2 * q);
@@ -557,7 +557,8 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   tjm::ProbDev P;
   std::memset(&P, 0, sizeof P);
   P.L = L; P.shift_ok = ctx->shift_ok; P.gemm_rule = ctx->opt.tile_rule; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
-  P.n_jumps = ctx->n_jumps; P.n_obs = n_obs; P.n_steps = R.n_steps; P.n_samples = n_times;
+  P.n_jumps = ctx->n_jumps; P.n_obs = n_obs1; P.n_obs2 = n_obs2; P.n_steps = R.n_steps; P.n_samples = n_times;
+  P.trotter_order = ctx->opt.trotter_order;
   P.dt = dt; P.trunc_eps = ctx->trunc_eps; P.krylov_tol = ctx->opt.krylov_tol;
   P.Dbond = ctx->d_Dbond;
   P.Wm1 = ctx->d_Wm1; P.Wm1_off = ctx->d_Wm1_off;
@@ -575,6 +576,15 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
     int* s = nullptr;
     if ((st = upload(ctx, R.bufs, sample_row.data(), sample_row.size(), &s))) return st;
     P.sample_row = s;
+    int* p2 = nullptr;
+    if ((st = upload(ctx, R.bufs, osite2.data(), osite2.size(), &p2))) return st;
+    P.osite2 = p2;
+    cx<double>* q2 = nullptr;
+    if ((st = upload(ctx, R.bufs, reinterpret_cast<const cx<double>*>(oop2.data()), oop2.size(), &q2))) return st;
+    P.oop2 = q2;
+    int* h2 = nullptr;
+    if ((st = upload(ctx, R.bufs, has2.data(), has2.size(), &h2))) return st;
+    P.site_has2 = h2;
   }
   if ((st = upload(ctx, R.bufs, &P, 1, &R.prob))) return st;
   // slots
@@ -623,7 +633,13 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
 
 tjm_status tjm_run_prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
                            const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id) {
-  return prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, times, n_times, run_id);
+  return prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, nullptr, 0, times, n_times, run_id);
+}
+
+tjm_status tjm_run_prepare2(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                            const tjm_observable* obs, int n_obs, const tjm_observable2* obs2, int n_obs2,
+                            const double* times, int n_times, int64_t* run_id) {
+  return prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, obs2, n_obs2, times, n_times, run_id);
 }
 
 static Run* find_run(tjm_ctx* ctx, int64_t id) {
@@ -643,19 +659,19 @@ static tjm_status launch(tjm_ctx* ctx, tjm::SlotDev* const* order, int n, int* n
   switch (ctx->opt.precision) {
     case TJM_PREC_FP64:
       e = tjm::launch_f64(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims);
+                          ctx->sdims, ctx->opt.tensor_cores);
       break;
     case TJM_PREC_FP32_DEC32:
       e = tjm::launch_f32d32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                             ctx->scratch_stride, ctx->sdims);
+                             ctx->scratch_stride, ctx->sdims, ctx->opt.tensor_cores);
       break;
     case TJM_PREC_FP32_DF64:
       e = tjm::launch_f32df(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                            ctx->scratch_stride, ctx->sdims);
+                            ctx->scratch_stride, ctx->sdims, ctx->opt.tensor_cores);
       break;
     default:
       e = tjm::launch_f32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims);
+                          ctx->sdims, ctx->opt.tensor_cores);
       break;
   }
   if (e != cudaSuccess) return fail(ctx, TJM_ECUDA, "advance kernel launch: %s", cudaGetErrorString(e));
@@ -731,7 +747,16 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
 
 tjm_status tjm_run(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
                    const tjm_observable* obs, int n_obs, const double* times, int n_times, int64_t* run_id) {
-  tjm_status st = prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, times, n_times, run_id);
+  tjm_status st = prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, nullptr, 0, times, n_times, run_id);
+  if (st) return st;
+  Run* R = find_run(ctx, *run_id);
+  return tjm_run_advance(ctx, *run_id, R->n_steps + 1);
+}
+
+tjm_status tjm_run2(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, int64_t first_traj, uint64_t seed,
+                    const tjm_observable* obs, int n_obs, const tjm_observable2* obs2, int n_obs2, const double* times,
+                    int n_times, int64_t* run_id) {
+  tjm_status st = prepare(ctx, psi0, n_traj, first_traj, seed, obs, n_obs, obs2, n_obs2, times, n_times, run_id);
   if (st) return st;
   Run* R = find_run(ctx, *run_id);
   return tjm_run_advance(ctx, *run_id, R->n_steps + 1);

@@ -9,6 +9,7 @@
 // block of complex accumulators in the working precision.
 #pragma once
 #include "tjm_common.cuh"
+#include "tjm_tc.cuh"
 
 namespace tjm {
 
@@ -145,6 +146,15 @@ __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alp
 // autotuner from timed launches.
 __shared__ int gemm_tile_rule;
 
+// Tensor-core state of the CTA (tjm_tc.cuh).  When enabled, every FP32 GEMM of
+// at least kTcMinWork complex multiply-adds runs on the tensor cores; smaller
+// ones (chain ends, tiny bonds) stay on the CUDA cores, where one 128-row MMA
+// tile would be mostly padding.
+__shared__ tc::Ctl tc_ctl;
+constexpr long long kTcMinWork = 16384;
+
+__device__ __forceinline__ bool use_tc(long long work) { return tc_ctl.enabled && work >= kTcMinWork; }
+
 template <class T, bool AK, bool BJ>
 __device__ __forceinline__ void gemm_layout(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* A, int sai,
                                             int sak, int ca, long long sa, const cx<T>* B, int sbk, int sbj, int cb,
@@ -164,6 +174,20 @@ __device__ __forceinline__ void blk_gemm_batched(int batch, int M, int N, int K,
                                                  long long sa, MatB<T> B, long long sb, cx<T>* C, long long sci,
                                                  long long scj, long long sc, bool accumulate, char* smem) {
   if (M <= 0 || N <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (K > 0 && use_tc((long long)M * N * K)) {
+      tc::TcA ta = {};
+      ta.si = A.si; ta.sk = A.sk; ta.conj = A.conj;
+      tc::TcB tb = {};
+      tb.sk = B.sk; tb.sj = B.sj; tb.conj = B.conj;
+      for (int b = 0; b < batch; ++b) {
+        ta.p = A.p + b * sa;
+        tb.p = B.p + b * sb;
+        tc::cgemm(&tc_ctl, M, N, K, alpha, ta, tb, C + b * sc, sci, scj, accumulate, smem);
+      }
+      return;
+    }
+  }
   const bool ak = A.sk == 1;
   const bool bj = (B.sj == 1) || (B.sk != 1);
   if (ak && bj)
@@ -270,9 +294,24 @@ __device__ __noinline__ void blk_wapply(int P, int O, int I, int Q, const cx<dou
 template <class T>
 __device__ __noinline__ void blk_wgemm(int P, int dd, int Dr, int I, int chr, const cx<double>* Wm,
                                        const cx<T>* __restrict__ t1, const cx<T>* R, cx<T>* y, char* smem,
-                                       double shift, int nsh, int so0, int so_step, int si0, int si_step) {
+                                       char* csr_global, double shift, int nsh, int so0, int so_step, int si0,
+                                       int si_step) {
   static_assert(sizeof(T) == 4, "fused MPO GEMM is for FP32 contractions");
   const int O = dd * Dr;
+  if (use_tc((long long)P * dd * chr * Dr * chr)) {
+    // the tensor cores own the shared staging area: the row-sparse block goes to global scratch (L1-resident)
+    wcsr_build<T>(O, I, Wm, csr_global, shift, nsh, so0, so_step, si0, si_step);
+    tc::TcA ta = {};
+    ta.fused = 1;
+    ta.val = reinterpret_cast<const cx<float>*>(csr_global);
+    ta.col = reinterpret_cast<const int*>(ta.val + O * I);
+    ta.rp = ta.col + O * I;
+    ta.t1 = t1; ta.sip = I * chr; ta.dd = dd; ta.Dr = Dr; ta.chr = chr;
+    tc::TcB tb = {};
+    tb.p = R; tb.sk = chr; tb.sj = 1;
+    tc::cgemm(&tc_ctl, P * dd, chr, Dr * chr, mk(1.f, 0.f), ta, tb, y, chr, 1, false, smem);
+    return;
+  }
   char* csr = smem + 2 * GB_K * 64 * (int)sizeof(cx<T>);
   wcsr_build<T>(O, I, Wm, csr, shift, nsh, so0, so_step, si0, si_step);
   WaArgs<T> wa;

@@ -6,18 +6,18 @@
 namespace tjm {
 
 cudaError_t launch_f32(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                      char* scratch, long long stride, ScratchDims dims) {
+                      char* scratch, long long stride, ScratchDims dims, int use_tc) {
   auto kern = advance_kernel<float, double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double>());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, double>());
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<double>(), s>>>(order, n, next, max_steps, scratch, stride, dims);
+  kern<<<ctas, TJM_THREADS, smem_bytes<float, double>(), s>>>(order, n, next, max_steps, scratch, stride, dims, use_tc);
   return cudaGetLastError();
 }
 
 int occupancy_f32() {
   int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, double>, TJM_THREADS, smem_bytes<double>());
+  cudaFuncSetAttribute(advance_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, double>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, double>, TJM_THREADS, smem_bytes<float, double>());
   return per_sm;
 }
 

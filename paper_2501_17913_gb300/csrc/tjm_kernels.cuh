@@ -18,10 +18,14 @@ namespace tjm {
 // (to size the allocation) and on the device (to carve it).
 struct ScratchMap {
   long long krylov, w, t1, t2, theta, tmp, bond, E, F, xsites, xchi;
-  long long da, du, dv, dvw, drd, dtau, ds, iw, G, wts, total;
+  long long da, du, dv, dvw, drd, dtau, ds, iw, G, G2, wts, wcsr, total;
 };
 
 __host__ __device__ inline long long align256(long long x) { return (x + 255) & ~255LL; }
+
+// row-sparse MPO block of a fused matvec when the tensor cores own the shared
+// staging area: values (<= 32 x 32 complex), columns and row pointers
+constexpr long long kWcsrBytes = 32 * 32 * 16 + 32 * 32 * 4 + 33 * 4;
 
 __host__ __device__ inline ScratchMap scratch_map(const ScratchDims& d, int szc, int szd) {
   // szc / szd: bytes of one complex element in the contraction / decomposition precision
@@ -49,19 +53,28 @@ __host__ __device__ inline ScratchMap scratch_map(const ScratchDims& d, int szc,
   m.ds = take(mm * szd);
   m.iw = take(2 * mm * 4);
   m.G = take((long long)d.Lmax * 4 * 16);
+  m.G2 = take((long long)d.Lmax * 16 * 16);
   m.wts = take((long long)(d.jmax + 1) * 8);
+  m.wcsr = take(kWcsrBytes);
   m.total = o;
   return m;
 }
 
-// Dynamic shared memory: GEMM staging, reductions, scalars, and -- for the
-// FP32 factorization precision -- a 64 KB workspace that holds the QR / SVD
-// matrix of a one-site update (up to 128 x 64 complex) plus its singular values.
-// FP64 factorizations keep their workspace in global memory and leave the
-// rest of the SM's L1 to cache it.
-constexpr int kSmemBase = kSmemGemm + 512 * 8 + 512 * 8;
+// Dynamic shared memory, in this order: reduction scratch (4 KB), scalars
+// (4 KB), the CUDA-core GEMM staging area (32 KB) and, for FP32 contractions,
+// 64 KB more plus 1 KB of singular values.  The 96 KB from the GEMM staging
+// area on are the tensor cores' operand stages when they run the
+// contractions; the 64 KB part is also the factorization workspace of an
+// FP32 QR / SVD (up to 128 x 64 complex), which never runs while a GEMM is in
+// flight.  FP64 contractions use the first 40 KB only and leave the rest of
+// the SM's L1 to cache their global workspaces.
+constexpr int kSmemRedOff = 0;
+constexpr int kSmemGsmOff = 8192;
+constexpr int kSmemFsmOff = kSmemGsmOff + kSmemGemm;
 constexpr int kFsmBytes = 65536;
-template <class Td> constexpr int smem_bytes() { return sizeof(Td) == 4 ? kSmemBase + kFsmBytes + 1024 : kSmemBase; }
+constexpr int kSmemFsvOff = kSmemFsmOff + kFsmBytes;
+static_assert(kSmemFsvOff - kSmemGsmOff >= tc::kSmemBytes, "tensor-core stages fit the GEMM and factorization areas");
+template <class Tc, class Td> constexpr int smem_bytes() { return sizeof(Tc) == 4 ? kSmemFsvOff + 1024 : kSmemFsmOff; }
 
 template <class Tc, class Td>
 __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDims& dims, char* smem) {
@@ -95,14 +108,16 @@ __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDim
   c.ds = reinterpret_cast<Td*>(scr + mp.ds);
   c.iw = reinterpret_cast<int*>(scr + mp.iw);
   c.G = reinterpret_cast<cx<double>*>(scr + mp.G);
+  c.G2 = reinterpret_cast<cx<double>*>(scr + mp.G2);
   c.wts = reinterpret_cast<double*>(scr + mp.wts);
-  c.gsm = smem;
-  c.red = reinterpret_cast<double*>(smem + kSmemGemm);
+  c.wcsr = scr + mp.wcsr;
+  c.gsm = smem + kSmemGsmOff;
+  c.red = reinterpret_cast<double*>(smem + kSmemRedOff);
   c.sc = c.red + 512;
   if (sizeof(Td) == 4) {
-    c.fsm = smem + kSmemBase;
+    c.fsm = smem + kSmemFsmOff;
     c.fsm_bytes = kFsmBytes;
-    c.fsv = smem + kSmemBase + kFsmBytes;
+    c.fsv = smem + kSmemFsvOff;
   } else {
     c.fsm = nullptr;
     c.fsm_bytes = 0;
@@ -160,11 +175,22 @@ __device__ bool init_state(const Ctx<Tc, Td>& c) {
 // The sampling layer and the main-branch jump of step j (Eq. SimulationStep):
 // measure J'(D[dt/2] X) on a copy if j is an output step, then
 // Phi_j = J(D[dt] X) while j < n.  X is the slot's MPS on entry.
+//
+// First-order baseline (trotter_order 1): Phi_j = J(D[dt] X) for every j, and
+// Psi(j dt) = Phi_j is measured directly.
 template <class Tc, class Td>
 __device__ bool finish_step(const Ctx<Tc, Td>& c, int j, bool sample) {
   const ProbDev* P = c.P;
   SlotDev* S = c.S;
   bool ok = true;
+  if (P->trotter_order == 1) {
+    double u1, u2;
+    tjm_uniforms(S->seed, S->traj_id, (uint32_t)j, 0, &u1, &u2);
+    TJM_TIMED(c, PH_DJ, ok = dissipate_jump(c, c.mps, P->Dfull, u1, u2));
+    if (ok && sample && P->sample_row[j] >= 0) TJM_TIMED(c, PH_MEASURE, measure(c, c.mps, P->sample_row[j]));
+    if (ok && j < P->n_steps) TJM_TIMED(c, PH_ENVBUILD, build_right_envs(c));
+    return ok;
+  }
   if (sample && P->sample_row[j] >= 0) {
     copy_mps(c, c.xmps, c.mps);
     double u1, u2;
@@ -201,9 +227,11 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
     ok = init_state(c);
     if (ok && P->sample_row[0] >= 0) measure(c, c.mps, P->sample_row[0]);
     if (ok && P->n_steps > 0) {
-      double u1, u2;
-      tjm_uniforms(S->seed, S->traj_id, 0, 0, &u1, &u2);
-      ok = dissipate_jump(c, c.mps, P->Dhalf, u1, u2);
+      if (P->trotter_order != 1) {      // F_0 = J(D[dt/2] .) of the Strang-split method
+        double u1, u2;
+        tjm_uniforms(S->seed, S->traj_id, 0, 0, &u1, &u2);
+        ok = dissipate_jump(c, c.mps, P->Dhalf, u1, u2);
+      }
       if (ok) build_right_envs(c);
     }
     step = 0;
@@ -238,6 +266,7 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
     }
   }
   __syncthreads();
+  if (tc_ctl.failed) ok = false;     // a bounded tensor-core wait ran out: results are not trustworthy
   if (threadIdx.x == 0) {
     S->step = step;
     S->flags = flags;
@@ -246,13 +275,17 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   __syncthreads();
 }
 
+// use_tc: FP32 contractions on the tensor cores (tcgen05); ignored for FP64
+// contractions.  The CTA holds its tensor-memory accumulator for the whole
+// persistent launch.
 template <class Tc, class Td>
 __global__ void __launch_bounds__(TJM_THREADS, TJM_MIN_BLOCKS)
 advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, char* scratch, long long stride,
-               ScratchDims dims) {
-  extern __shared__ __align__(16) char smem[];
+               ScratchDims dims, int use_tc) {
+  extern __shared__ __align__(1024) char smem[];
   __shared__ int sid;
   char* scr = scratch + (long long)blockIdx.x * stride;
+  tc::cta_setup(&tc_ctl, sizeof(Tc) == 4 && use_tc);
   for (;;) {
     if (threadIdx.x == 0) sid = atomicAdd(next, 1);
     __syncthreads();
@@ -261,6 +294,7 @@ advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, cha
     if (s >= n_slots) break;
     run_slot<Tc, Td>(order[s], max_steps, scr, dims, smem);
   }
+  tc::cta_teardown(&tc_ctl);
 }
 
 }  // namespace tjm

@@ -10,7 +10,7 @@ namespace tjm {
 
 #define TJM_DECLARE_LAUNCH(NAME)                                                                              \
   cudaError_t launch_##NAME(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas, \
-                            char* scratch, long long stride, ScratchDims dims);                               \
+                            char* scratch, long long stride, ScratchDims dims, int use_tc);                               \
   int occupancy_##NAME();
 
 TJM_DECLARE_LAUNCH(f64)

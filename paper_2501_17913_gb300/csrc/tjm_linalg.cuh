@@ -299,7 +299,11 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         const T ag = cabs_scaled(ga);
         if (!(ag > tol * sqrt(al) * sqrt(be))) continue;
         const T zeta = (be - al) / ((T)2 * ag);
-        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+        // tan of the rotation angle, sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); beyond |zeta| = 1e8 it is
+        // sign(zeta) / (2 |zeta|) to within 1e-16 relative, which also keeps zeta^2 from overflowing the
+        // FP32 exponent range of double-float
+        const T az = fabs(zeta);
+        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (az > T(1e8f) ? (T)2 * az : az + sqrt((T)1 + zeta * zeta));
         const T c = (T)1 / sqrt((T)1 + t * t), sn = c * t;
         const cx<T> ph = mk(ga.x / ag, -ga.y / ag);           // e^{-i phi}
         // [a_p, a_q] <- [a_p, a_q] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]

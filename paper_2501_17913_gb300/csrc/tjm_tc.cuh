@@ -230,7 +230,7 @@ __device__ __forceinline__ cx<float> tc_loadB(const TcB& b, int K, int N, int k,
 // C = alpha A B (+ C).  M, N, K > 0; C(i, j) at c[i * sci + j * scj].  All
 // threads of the CTA call it; smem is the 96 KB staging area (16-byte
 // aligned).  Returns false if a wait timed out (results are then undefined).
-__device__ __noinline__ bool cgemm(Ctl* ctl, int M, int N, int K, cx<float> alpha, TcA A, TcB B, cx<float>* C,
+static __device__ __noinline__ bool cgemm(Ctl* ctl, int M, int N, int K, cx<float> alpha, TcA A, TcB B, cx<float>* C,
                                    long long sci, long long scj, bool accumulate, char* smem) {
   if (ctl->failed) return false;
   const int tid = threadIdx.x;

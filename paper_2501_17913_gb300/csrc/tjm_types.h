@@ -28,6 +28,12 @@ struct ProbDev {
   const int* osite;                       // [n_obs]
   const cx<double>* oop;                  // [n_obs][4]
   const int* sample_row;                  // [n_steps + 1] -> output row or -1
+  // two-site observables on (osite2, osite2 + 1), written after the one-site ones in each output row
+  int n_obs2;
+  const int* osite2;                      // [n_obs2]
+  const cx<double>* oop2;                 // [n_obs2][16], row (t1 t2), column (s1 s2)
+  const int* site_has2;                   // [L]: 1 if some two-site observable starts at the site
+  int trotter_order;                      // 2: the Strang-split TJM; 1: the first-order baseline
 };
 
 struct SlotStats {

@@ -66,6 +66,28 @@ def z_observables(L: int):
     return [(l, Z.copy()) for l in range(L)]
 
 
+def xx_observables(L: int):
+    """Nearest-neighbour correlators X_i X_{i+1} (paper Fig. 4b) as two-site operators on (i, i+1)."""
+    return [(l, np.kron(X, X)) for l in range(L - 1)]
+
+
+def tfim_mpo(L: int, J: float = 1.0, g: float = 1.0):
+    """MPO (bond dimension 3) of the transverse-field Ising chain H = -J sum_i Z_i Z_{i+1} - g sum_j X_j
+    (paper Sec. "Benchmarking", critical point J = g = 1).  Same layout as xxx_mpo."""
+    Wb = np.zeros((3, 3, 2, 2), dtype=np.complex128)
+    Wb[0, 0] = I2
+    Wb[0, 1] = -J * Z
+    Wb[0, 2] = -g * X
+    Wb[1, 2] = Z
+    Wb[2, 2] = I2
+    if L == 1:
+        return [Wb[0:1, 2:3].copy()]
+    W = [Wb[0:1, :].copy()]
+    W += [Wb.copy() for _ in range(L - 2)]
+    W.append(Wb[:, 2:3].copy())
+    return W
+
+
 def all_zero(L: int):
     return [np.array([1.0, 0.0], dtype=np.complex128) for _ in range(L)]
 
@@ -204,6 +226,25 @@ def request_stream(seed: int = 11, n_requests: int = 200, rate: float = 20.0):
         out.append((t, Workload(f'req{r}', xxx_mpo(L, 1.0, gfield), noise(L, gam, gam), dt, n, chi, 1e-10,
                                 N, seed * 1000003 + r, neel(L), z_observables(L), [n])))
     return out
+
+
+def edge_driven_xxx(L: int = 100, eps: float = 10 * math.pi, chi_max: int = 4, n_traj: int = 100, T: float = 100.0,
+                    dt: float = 0.1, sample_every: int = 10, seed: int = 3) -> Workload:
+    """The boundary-driven XXX chain of the paper's large-scale validation (Sec. "Validating convergence
+    against analytical results"): H = -J sum_i (X X + Y Y + Z Z) - h sum_j Z_j with J = 1, h = 0, jump
+    operators sqrt(eps) sigma^+ on the first site and sqrt(eps) sigma^- on the last, |0...0> start, dt = 0.1.
+
+    That section defines sigma^+- = (X +- i Y) / 2, so its sigma^+ is [[0, 1], [0, 0]] (our SM: it pumps
+    the first site to |0>, Z = +1) and its sigma^- is [[0, 0], [1, 0]] (our SP: the last site to |1>,
+    Z = -1), which is the orientation of the stated steady state <Z_j> = cos(pi (j - 1) / (L - 1)).
+    """
+    n = int(round(T / dt))
+    samples = list(range(0, n + 1, sample_every))
+    if samples[-1] != n:
+        samples.append(n)
+    return Workload(f'edge_driven_L{L}_chi{chi_max}', xxx_mpo(L, -1.0, 0.0), [(0, SM.copy(), float(eps)),
+                    (L - 1, SP.copy(), float(eps))], dt, n, chi_max, 1e-10, n_traj, seed, all_zero(L),
+                    z_observables(L), samples)
 
 
 def random_mps(L: int, chi_max: int, seed: int = 1234):

@@ -33,6 +33,10 @@ class tjm_observable(C.Structure):
     _fields_ = [("site", C.c_int), ("op", C.c_double * 8)]
 
 
+class tjm_observable2(C.Structure):
+    _fields_ = [("site", C.c_int), ("op", C.c_double * 32)]
+
+
 class tjm_state(C.Structure):
     _fields_ = [("kind", C.c_int), ("data", C.POINTER(C.c_double)), ("chi", C.POINTER(C.c_int))]
 
@@ -40,7 +44,8 @@ class tjm_state(C.Structure):
 class tjm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int),
-                ("energy_shift", C.c_int), ("tile_rule", C.c_int)]
+                ("energy_shift", C.c_int), ("tile_rule", C.c_int), ("tensor_cores", C.c_int),
+                ("trotter_order", C.c_int)]
 
 
 class tjm_stats(C.Structure):
@@ -70,6 +75,12 @@ SIGNATURES = [
     ("tjm_run_prepare", C.c_int, [C.c_void_p, C.POINTER(tjm_state), C.c_int64, C.c_int64, C.c_uint64,
                                   C.POINTER(tjm_observable), C.c_int, C.POINTER(C.c_double), C.c_int,
                                   C.POINTER(C.c_int64)]),
+    ("tjm_run_prepare2", C.c_int, [C.c_void_p, C.POINTER(tjm_state), C.c_int64, C.c_int64, C.c_uint64,
+                                   C.POINTER(tjm_observable), C.c_int, C.POINTER(tjm_observable2), C.c_int,
+                                   C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int64)]),
+    ("tjm_run2", C.c_int, [C.c_void_p, C.POINTER(tjm_state), C.c_int64, C.c_int64, C.c_uint64,
+                           C.POINTER(tjm_observable), C.c_int, C.POINTER(tjm_observable2), C.c_int,
+                           C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int64)]),
     ("tjm_run_advance", C.c_int, [C.c_void_p, C.c_int64, C.c_int]),
     ("tjm_run_group_advance", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int, C.c_int]),
     ("tjm_poll", C.c_int, [C.c_void_p, C.c_int64]),
@@ -96,6 +107,9 @@ SIGNATURES = [
     ("tjm_selftest_svd", C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("tjm_selftest_tc_cgemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("tjm_selftest_contract", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("tjm_selftest_expm_tridiag", C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
                                             C.POINTER(C.c_double)]),
@@ -150,7 +164,8 @@ class Context:
     """One TJM problem (tjm_create) and the runs started on it."""
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32_DF64, krylov_max=30, krylov_tol=0.0,
-                 exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0):
+                 exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0, tensor_cores=True,
+                 trotter_order=2):
         lib = load()
         self.lib = lib
         L = len(W)
@@ -169,6 +184,8 @@ class Context:
         opt.exact_full_bond, opt.device, opt.max_ctas = int(bool(exact)), device, max_ctas
         opt.energy_shift = int(bool(energy_shift))
         opt.tile_rule = int(tile_rule)
+        opt.tensor_cores = int(bool(tensor_cores))
+        opt.trotter_order = int(trotter_order)
         h = C.c_void_p()
         st = lib.tjm_create(C.byref(h), C.byref(mpo), js, len(jumps), float(dt), int(chi_max), float(trunc_eps),
                             C.byref(opt))
@@ -205,18 +222,33 @@ class Context:
         return tjm_state(kind, _dp(data), None), keep
 
     def prepare(self, psi0, n_traj, seed, observables, times, first_traj=0, launch=False):
+        """observables: [(site, op)] with op 2 x 2 (one site) or 4 x 4 (sites site, site + 1); results come
+        back in the caller's order."""
         st_, keep = self._state(psi0, n_traj)
-        obs = (tjm_observable * max(1, len(observables)))()
-        for i, (site, op) in enumerate(observables):
-            obs[i].site = int(site)
-            obs[i].op = _op8(op)
+        one = [(i, s_, o) for i, (s_, o) in enumerate(observables) if np.shape(o) == (2, 2)]
+        two = [(i, s_, o) for i, (s_, o) in enumerate(observables) if np.shape(o) == (4, 4)]
+        if len(one) + len(two) != len(observables):
+            raise ValueError("observables must be 2 x 2 or 4 x 4")
+        obs = (tjm_observable * max(1, len(one)))()
+        for k, (_, site, op) in enumerate(one):
+            obs[k].site = int(site)
+            obs[k].op = _op8(op)
+        obs2 = (tjm_observable2 * max(1, len(two)))()
+        for k, (_, site, op) in enumerate(two):
+            obs2[k].site = int(site)
+            flat = np.stack([np.asarray(op).real, np.asarray(op).imag], axis=-1).reshape(-1)
+            for q in range(32):
+                obs2[k].op[q] = float(flat[q])
         t = np.ascontiguousarray(np.asarray(times, dtype=np.float64))
         rid = C.c_int64()
-        f = self.lib.tjm_run if launch else self.lib.tjm_run_prepare
-        st = f(self.h, C.byref(st_), int(n_traj), int(first_traj), C.c_uint64(seed), obs, len(observables), _dp(t),
-               len(t), C.byref(rid))
+        f = self.lib.tjm_run2 if launch else self.lib.tjm_run_prepare2
+        st = f(self.h, C.byref(st_), int(n_traj), int(first_traj), C.c_uint64(seed), obs, len(one), obs2, len(two),
+               _dp(t), len(t), C.byref(rid))
         self._check(st, "tjm_run" if launch else "tjm_run_prepare")
-        self.runs[rid.value] = (int(n_traj), len(t), len(observables))
+        # device column of each caller observable: the one-site ones first, then the two-site ones
+        order = [i for (i, _, _) in one] + [i for (i, _, _) in two]
+        inv = np.argsort(order) if order else np.zeros(0, dtype=int)
+        self.runs[rid.value] = (int(n_traj), len(t), len(observables), inv)
         return rid.value
 
     def run(self, psi0, n_traj, seed, observables, times, first_traj=0):
@@ -241,13 +273,17 @@ class Context:
         return True
 
     def result(self, run_id, per_traj=True, allow_numeric=False):
-        n_traj, n_t, n_o = self.runs[run_id]
+        n_traj, n_t, n_o, inv = self.runs[run_id]
         mean = np.zeros((n_t, n_o))
         sem = np.zeros((n_t, n_o))
         pt = np.zeros((n_traj, n_t, n_o)) if per_traj else None
         st = self.lib.tjm_result(self.h, run_id, _dp(mean), _dp(sem), _dp(pt))
         if not (allow_numeric and st == TJM_ENUMERIC):
             self._check(st, "tjm_result")
+        if n_o:
+            mean, sem = mean[:, inv], sem[:, inv]
+            if pt is not None:
+                pt = pt[:, :, inv]
         return mean, sem, pt
 
     def stats(self, run_id):
@@ -384,6 +420,36 @@ def selftest_tc_cgemm(A, B, conj_a=False, conj_b=False, a_col_major=False, b_k_c
                                    _dp(_cplx(A)), _dp(_cplx(B)), _dp(out))
     if st != TJM_OK:
         raise TJMError(st, "tjm_selftest_tc_cgemm")
+    return _z(out)
+
+
+def selftest_contract(kind, precision, Lenv, Renv, x, W1=None, W2=None, tensor_cores=True):
+    """One effective-Hamiltonian application (kind 0 bond, 1 one site, 2 two sites) or environment update
+    (3 left, 4 right) by the trajectory kernel's device functions; layouts as in tjm_selftest_contract."""
+    lib = load()
+    Lenv = np.asarray(Lenv, dtype=np.complex128)
+    Renv = np.asarray(Renv, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.complex128)
+    if kind == 4:
+        chl, chr_ = x.shape[0], x.shape[-1]
+        Dl, Dr = np.shape(W1)[0], np.shape(W1)[1]
+        Du = 1
+    else:
+        chl = Lenv.shape[0]
+        Dl = Lenv.shape[1]
+        chr_ = Renv.shape[2] if kind != 3 else x.shape[-1]
+        Dr = Renv.shape[0] if kind in (1, 2) else (np.shape(W1)[1] if kind == 3 else Dl)
+        Du = np.shape(W1)[1] if kind == 2 else 1
+    shape = {0: (chl, chr_), 1: (chl, 2, chr_), 2: (chl, 2, 2, chr_), 3: (chr_, Dr, chr_), 4: (Dl, chl, chl)}[kind]
+    out = np.zeros(shape + (2,))
+    w1 = _cplx(W1) if W1 is not None else None
+    w2 = _cplx(W2) if W2 is not None else None
+    rin = _cplx(Renv) if kind != 3 else np.zeros(2)
+    lin = _cplx(Lenv) if kind != 4 else np.zeros(2)
+    st = lib.tjm_selftest_contract(int(kind), int(precision), int(bool(tensor_cores)), int(chl), int(chr_), int(Dl),
+                                   int(Du), int(Dr), _dp(w1), _dp(w2), _dp(lin), _dp(rin), _dp(_cplx(x)), _dp(out))
+    if st != TJM_OK:
+        raise TJMError(st, "tjm_selftest_contract")
     return _z(out)
 
 

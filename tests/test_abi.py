@@ -43,7 +43,7 @@ def test_default_options(lib):
     lib.tjm_default_options(C.byref(o))
     assert (o.precision, o.krylov_max, o.krylov_tol, o.exact_full_bond, o.device, o.max_ctas) == \
            (tjm.PREC_FP32_DF64, 30, 0.0, 0, 0, 0)
-    assert (o.energy_shift, o.tile_rule) == (1, 0)
+    assert (o.energy_shift, o.tile_rule, o.tensor_cores, o.trotter_order) == (1, 0, 1, 2)
 
 
 @pytest.mark.parametrize("case", ["dt", "chi_low", "chi_high", "eps", "one_site", "open_end", "precision",
@@ -81,6 +81,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     if not cc:
         pytest.skip("no C compiler")
     structs = {"tjm_mpo": tjm.tjm_mpo, "tjm_jump": tjm.tjm_jump, "tjm_observable": tjm.tjm_observable,
+               "tjm_observable2": tjm.tjm_observable2,
                "tjm_state": tjm.tjm_state, "tjm_options": tjm.tjm_options, "tjm_stats": tjm.tjm_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tjm.h"', "int main(void) {"]
     for name, cls in structs.items():
