@@ -49,6 +49,10 @@ def parse():
                    help="trajectories of the plain-FP64 GPU arm (0: one per SM; see DESIGN, FP64 is pipe-bound)")
     p.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end tjm_run measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--serve-requests", type=int, default=8,
+                   help="serving replay: the first R arrivals of the Poisson request stream (0: skip)")
+    p.add_argument("--serve-traj-scale", type=float, default=1.0 / 64)
+    p.add_argument("--serve-max-steps", type=int, default=10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--ref-sites", type=int, default=200,
                    help="reference arm: sites of the chi-saturated chain each oracle trajectory steps through")
@@ -243,6 +247,31 @@ def profiled_traffic(kernel_file, units_per_launch):
     return float(per.group(1)) * units_per_launch, "profiles/%s scaled by units" % kernel_file
 
 
+# ----------------------------------------------------------------------------- serving replay
+def run_serving(a, prec, device):
+    """Replay the first --serve-requests arrivals of the Poisson stream (20 req/s, seed 11) through the
+    continuous-batching loop, each request's trajectory count scaled by --serve-traj-scale and its step
+    count capped at --serve-max-steps; p50 / p99 completion latency, offered and sustained load."""
+    import math as _m
+    from paper_2501_17913_gb300 import inputs as I
+    from paper_2501_17913_gb300.serve import Server
+    stream = I.request_stream()[:a.serve_requests]
+    srv = Server(precision=prec, steps_per_tick=1, device=device)
+    t0 = time.perf_counter()
+    for (t_arr, wl) in stream:
+        wl.n_traj = max(1, int(_m.ceil(wl.n_traj * a.serve_traj_scale)))
+        wl.n_steps = min(wl.n_steps, a.serve_max_steps)
+        wl.sample_steps = [wl.n_steps]
+        srv.submit(wl, t0 + t_arr)
+    srv.drain()
+    t1 = time.perf_counter()
+    rep = srv.report(t0, t1)
+    rep["stream"] = ("first %d arrivals of the Poisson stream (20/s, seed 11), trajectory counts x %.4g, at most %d "
+                     "steps each" % (a.serve_requests, a.serve_traj_scale, a.serve_max_steps))
+    srv.close()
+    return rep
+
+
 # ----------------------------------------------------------------------------- ours (GPU)
 def main():
     a = parse()
@@ -387,6 +416,9 @@ def main():
                                       "bench's seed), FP64 contractions and factorizations" % (N64, L, chi),
                              "ms": ms64}
         ctx3.close()
+    serving = None
+    if a.serve_requests > 0 and rank == 0:
+        serving = run_serving(a, prec, local)
     cpu = None
     if not a.no_cpu and rank == 0:
         cpu = oracle_sample(max(1, min(os.cpu_count() or 1, 16)), min(L, a.ref_sites), chi)
@@ -402,7 +434,7 @@ def main():
                "config": workload_config(a, world, 8 if prec else 16),
                "roofline": roof, "clocks": clocks, "gpu_launches": gpu_launches,
                "tile_autotune": {"rule": rule, "trials": tuner.report()},
-               "e2e": e2e, "cpu_baseline": cpu,
+               "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
                "stats": {"jumps": s1["jumps"] - s0["jumps"],
                          "matvecs_one_site": s1["matvec_one_site"] - s0["matvec_one_site"],
                          "matvecs_bond": s1["matvec_bond"] - s0["matvec_bond"],

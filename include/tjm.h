@@ -130,6 +130,10 @@ typedef struct {
                          * Trotterization", Eq. SimulationStep).  1: the first-order baseline the paper
                          * compares with (Fig. 4a, dotted): Phi_j = J(D[dt] U[dt] Phi_{j-1}) from
                          * Phi_0 = Psi(0), and Psi(j dt) = Phi_j is measured directly. */
+  int projection_error; /* 1: every output row gets one more column, the projection error of 1TDVP
+                         * ||(I - P) H |Psi>|| at the measured state (Sec. "Error measures"), computed by
+                         * a diagnostic sweep that uses the two-site tangent space (exact for MPOs with
+                         * nearest-neighbour terms).  Default 0. */
 } tjm_options;
 
 /* Fill opts with the defaults above. */
@@ -185,8 +189,15 @@ tjm_status tjm_run_advance(tjm_ctx* ctx, int64_t run_id, int max_steps);
 /* tjm_run_group_advance -- one persistent kernel over the trajectories of
  * several runs (possibly of different contexts on the same device), each
  * moved forward by at most max_steps steps.  Work is ordered by estimated
- * cost (largest first).  Launched on the stream of ctxs[0]. */
+ * cost (largest first).  Launched on the stream of ctxs[0]; asynchronous (the
+ * work list lives in ctxs[0] and is refilled in stream order). */
 tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, int n_runs, int max_steps);
+
+/* tjm_scratch_bytes -- device bytes of the per-CTA scratch that a launch of
+ * this context's precision holds for trajectories of up to chi_cap and L
+ * sites (all resident CTAs together); it is allocated at the first launch
+ * that needs it and kept by the context.  For admission control by memory. */
+tjm_status tjm_scratch_bytes(const tjm_ctx* ctx, int chi_cap, int L, int64_t* bytes);
 
 /* tjm_poll -- TJM_OK if the run's device work has finished, TJM_EBUSY if not. */
 tjm_status tjm_poll(tjm_ctx* ctx, int64_t run_id);

@@ -164,6 +164,64 @@ def local_expectations(mps, ops):
     return np.array(vals), norm2
 
 
+def projection_error(mps, W):
+    """Projection error of 1TDVP at the state of `mps` (Sec. "Error measures"):
+    eps = || (I - P) H |psi> ||_2 for the normalised |psi>, with P the projector onto the tangent space
+    of the fixed-bond-dimension manifold at psi,
+        P = sum_{l=0}^{L-1} P_L(<l) (x) 1_l (x) P_R(>l)  -  sum_{l=0}^{L-2} P_L(<=l) (x) P_R(>l),
+    P_L(<l) the projector onto the span of the left block states of sites 0..l-1 and P_R(>l) onto the
+    right block states of sites l+1..L-1.  Written out densely (small L only): H from the MPO, the block
+    states from a left- and a right-canonical copy of the MPS.
+    """
+    from .dense import mpo_to_dense
+    L = len(mps)
+    d = mps[0].shape[1]
+    H = mpo_to_dense(W)
+    left = [np.array(m) for m in mps]
+    for l in range(L - 1):
+        qr_move_right(left, l)
+    right = [np.array(m) for m in mps]
+    for l in range(L - 1, 0, -1):
+        rq_move_left(right, l)
+    # psi from the right-canonical copy (centre at site 0), normalised
+    psi = right[0]
+    for M in right[1:]:
+        psi = np.tensordot(psi, M, ([psi.ndim - 1], [0]))
+    psi = psi.reshape(-1)
+    psi = psi / np.linalg.norm(psi)
+    # left block isometries BL[l]: (d^(l+1), chi_{l+1}); right block isometries BR[l]: (chi_l, d^(L-l))
+    BL = []
+    acc = np.ones((1, 1), dtype=np.complex128)
+    for l in range(L):
+        acc = np.tensordot(acc, left[l], ([1], [0])).reshape(-1, left[l].shape[2])
+        BL.append(acc)
+    BR = [None] * L
+    acc = np.ones((1, 1), dtype=np.complex128)
+    for l in range(L - 1, -1, -1):
+        acc = np.tensordot(right[l], acc.reshape(right[l].shape[2], -1), ([2], [0])).reshape(right[l].shape[0], -1)
+        BR[l] = acc
+
+    def PL(n):        # projector onto the left block states of sites 0..n-1
+        if n == 0:
+            return np.ones((1, 1))
+        B = BL[n - 1]
+        return B @ B.conj().T
+
+    def PR(n):        # projector onto the right block states of sites n..L-1
+        if n == L:
+            return np.ones((1, 1))
+        B = BR[n]
+        return B.conj().T @ B
+
+    P = np.zeros((d ** L, d ** L), dtype=np.complex128)
+    for l in range(L):
+        P += np.kron(np.kron(PL(l), np.eye(d)), PR(l + 1))
+    for l in range(L - 1):
+        P -= np.kron(PL(l + 1), PR(l + 1))
+    v = H @ psi
+    return float(np.linalg.norm(v - P @ v))
+
+
 def measure(mps, observables):
     """Re <O_i> = Re <psi|O_i|psi> / <psi|psi>  (Eq. TJMExpVal, one trajectory)."""
     vals, norm2 = local_expectations(mps, observables)
@@ -490,7 +548,7 @@ def padded_product_mps(phis, rng=None):
 # --------------------------------------------------------------------------
 # one trajectory (Sec. "Algorithm": sampling MPS Phi, F_0, F_j, F_n)
 # --------------------------------------------------------------------------
-def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sample_steps, order=2):
+def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sample_steps, order=2, on_sample=None):
     """Observables of one TJM trajectory at the sampled steps.
 
     Reading of the sampling-MPS indexing (Eqs. TimeEvolutionFunctions,
@@ -501,6 +559,7 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
     order=1 is the first-order baseline of Fig. 4a (dotted lines), read as the
     plain Lie-Trotter product with the same U, D and J: for j = 1..n
     Psi(j dt) = J(D[dt] U[dt] Psi((j-1) dt)) (branch 0), measured directly.
+    on_sample(j, state), if given, sees every measured state (e.g. for the projection error).
     Returns (values[n_sample, n_obs], stats).
     """
     mps = [np.array(m, dtype=np.complex128) for m in psi0]
@@ -524,6 +583,8 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
     sw = Sweeper(prob)
     if 0 in want:
         vals[0] = measure(mps, observables)
+        if on_sample:
+            on_sample(0, mps)
     if order == 1:
         for j in range(1, n_steps + 1):
             sw.build_right_envs(mps)
@@ -532,6 +593,8 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
             note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec), j)
             if j in want:
                 vals[j] = measure(mps, observables)
+                if on_sample:
+                    on_sample(j, mps)
     if order == 2 and n_steps > 0:
         u1, u2 = uniforms(seed, traj_id, 0, 0)
         note(dissipate_and_jump(mps, prob, D_half, u1, u2, sw.rec), 0)
@@ -543,6 +606,8 @@ def run_trajectory(prob: Problem, psi0, traj_id, seed, observables, n_steps, sam
             u1, u2 = uniforms(seed, traj_id, j, 1)
             note(dissipate_and_jump(X, prob, D_half, u1, u2, sw.rec), j)
             vals[j] = measure(X, observables)
+            if on_sample:
+                on_sample(j, X)
         if j < n_steps:
             u1, u2 = uniforms(seed, traj_id, j, 0)
             note(dissipate_and_jump(mps, prob, D_full, u1, u2, sw.rec), j)

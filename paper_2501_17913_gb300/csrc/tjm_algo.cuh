@@ -692,7 +692,7 @@ template <class Tc, class Td>
 __device__ void measure(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int row) {
   const ProbDev* P = c.P;
   local_blocks(c, m, P->n_obs2 > 0);
-  double* out = c.S->out + (long long)row * (P->n_obs + P->n_obs2);
+  double* out = c.S->out + (long long)row * P->n_cols;
   for (int o = threadIdx.x; o < P->n_obs; o += TJM_THREADS) {
     const int l = P->osite[o];
     const cx<double>* op = P->oop + 4 * o;
@@ -711,6 +711,48 @@ __device__ void measure(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int row) {
     out[P->n_obs + o] = v.x / (g[0].x + g[3].x);
   }
   __syncthreads();
+}
+
+// ------------------------------------------------------------------ projection error
+// eps = ||(I - P) H psi|| of 1TDVP at the normalised state m (Sec. "Error measures"), for an MPO with
+// nearest-neighbour terms, where the two-site tangent projector P2 already reproduces H psi:
+//   eps^2 = ||P2 H psi||^2 - ||P1 H psi||^2
+//         = sum_l ||H2_l Theta_l||^2 - sum_{0<l<L-1} ||H1_l A_l||^2 - sum_l ||H1_l A_l||^2 + sum_l ||H0_l C_l||^2
+// with A_l the centre tensor, C_l the bond matrix and Theta_l = A_l B_{l+1} of the mixed-canonical form
+// centred at l (the tangent projectors are sums of orthogonal parts, so their squared norms add).  One
+// left-to-right sweep with QR steps; m must be right-canonical with its centre at site 0 and is left
+// left-canonical (same state).  Uses the trajectory's environment arrays; the shifted MPO (H - E I) has
+// the same projection error, since psi lies in the tangent space, and keeps the sums small.
+template <class Tc, class Td>
+__device__ __noinline__ double projection_error(const Ctx<Tc, Td>& c0, const Mps<Tc>& m) {
+  Ctx<Tc, Td> c = c0;
+  c.mps = m;
+  const int L = c.P->L;
+  if (threadIdx.x == 0) { c.Renv(L)[0] = mk((Tc)1, (Tc)0); c.Lenv(0)[0] = mk((Tc)1, (Tc)0); }
+  __syncthreads();
+  for (int l = L - 1; l >= 1; --l) env_right(c, l);
+  double s1 = 0.0, s1i = 0.0, s2 = 0.0, s0 = 0.0;
+  for (int l = 0; l < L; ++l) {
+    const int chl = m.chi[l], chr = m.chi[l + 1];
+    heff1(c, l, m.site(l), c.w);
+    const double n1 = blk_nrm2sq(c.w, chl * kD * chr, c.red);
+    s1 += n1;
+    if (l > 0 && l < L - 1) s1i += n1;
+    if (l + 1 < L) {
+      const int chn = m.chi[l + 2];
+      blk_gemm<Tc>(chl * kD, kD * chn, chr, matA(m.site(l), chr, 1), matB(m.site(l + 1), kD * chn, 1), c.theta,
+                   kD * chn, 1, c.gsm);
+      heff2(c, l, chl, chn, c.theta, c.w);
+      s2 += blk_nrm2sq(c.w, chl * kD * kD * chn, c.red);
+      const int k = qr_right(c, m, l);
+      env_left(c, l);
+      heff0(c, l + 1, k, chr, c.bond, c.w);
+      s0 += blk_nrm2sq(c.w, k * chr, c.red);
+      absorb_right(c, m, l, chr);
+    }
+  }
+  const double e2 = s2 - s1i - s1 + s0;
+  return e2 > 0.0 ? sqrt(e2) : 0.0;
 }
 
 // ------------------------------------------------------------------ dissipation + jump

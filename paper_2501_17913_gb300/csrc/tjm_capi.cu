@@ -102,6 +102,10 @@ struct tjm_ctx {
   tjm::ScratchDims sdims = {0, 0, 0, 0, 0};
   std::map<int64_t, std::unique_ptr<Run>> runs;
   int64_t next_run = 1;
+  // work list and counter of group launches (tjm_run_group_advance), reused from launch to launch:
+  // the stream orders each refill after the previous kernel that reads it
+  DevBuf group_order;
+  DevBuf group_next;
   ~tjm_ctx() {
     runs.clear();
     for (DevBuf* b : pbufs) delete b;
@@ -269,6 +273,7 @@ void tjm_default_options(tjm_options* o) {
   o->tile_rule = 0;
   o->tensor_cores = 1;
   o->trotter_order = 2;
+  o->projection_error = 0;
 }
 
 const char* tjm_last_error(const tjm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -288,6 +293,7 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   if (o.tile_rule < 0 || o.tile_rule > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.trotter_order != 1 && o.trotter_order != 2) return fail(nullptr, TJM_EINVAL, "");
+  if (o.projection_error < 0 || o.projection_error > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.krylov_max <= 0 || o.krylov_max > 30) o.krylov_max = 30;
   if (!(o.krylov_tol > 0)) o.krylov_tol = o.precision == TJM_PREC_FP64 ? 1e-12 : 1e-7;
   const int L = H->L;
@@ -429,7 +435,8 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   if (!run_id || n_traj < 1 || n_traj > (1LL << 30) || first_traj < 0 || n_obs1 < 0 || (n_obs1 && !obs) ||
       n_obs2 < 0 || (n_obs2 && !obs2) || n_times < 1 || !times)
     return fail(ctx, TJM_EINVAL, "bad run arguments");
-  const int n_obs = n_obs1 + n_obs2;     // output columns: one-site observables, then two-site ones
+  // output columns: one-site observables, two-site ones, then the projection error if requested
+  const int n_obs = n_obs1 + n_obs2 + (ctx->opt.projection_error ? 1 : 0);
   TJM_CU(cudaSetDevice(ctx->device));
   const int L = ctx->L;
   const double dt = ctx->dt;
@@ -559,6 +566,8 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   P.L = L; P.shift_ok = ctx->shift_ok; P.gemm_rule = ctx->opt.tile_rule; P.chi_max = ctx->chi_max; P.exact = ctx->opt.exact_full_bond; P.krylov_max = ctx->opt.krylov_max;
   P.n_jumps = ctx->n_jumps; P.n_obs = n_obs1; P.n_obs2 = n_obs2; P.n_steps = R.n_steps; P.n_samples = n_times;
   P.trotter_order = ctx->opt.trotter_order;
+  P.proj_err = ctx->opt.projection_error ? 1 : 0;
+  P.n_cols = n_obs;
   P.dt = dt; P.trunc_eps = ctx->trunc_eps; P.krylov_tol = ctx->opt.krylov_tol;
   P.Dbond = ctx->d_Dbond;
   P.Wm1 = ctx->d_Wm1; P.Wm1_off = ctx->d_Wm1_off;
@@ -628,6 +637,14 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   const int64_t id = ctx->next_run++;
   ctx->runs[id] = std::move(run);
   *run_id = id;
+  return TJM_OK;
+}
+
+tjm_status tjm_scratch_bytes(const tjm_ctx* ctx, int chi_cap, int L, int64_t* bytes) {
+  if (!ctx || !bytes || chi_cap < 1 || chi_cap > 64 || L < 1) return TJM_EINVAL;
+  tjm::ScratchDims d = {chi_cap, ctx->Dmax, ctx->opt.krylov_max, L, ctx->n_jumps};
+  const tjm::ScratchMap mp = tjm::scratch_map(d, (int)szc_of(ctx->opt.precision), (int)szd_of(ctx->opt.precision));
+  *bytes = (int64_t)mp.total * resident(const_cast<tjm_ctx*>(ctx));
   return TJM_OK;
 }
 
@@ -727,12 +744,23 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
   ord.reserve((size_t)total);
   for (auto& pr : rs)
     for (int64_t t = 0; t < pr.second->n_traj; ++t) ord.push_back(pr.second->slots + t);
-  std::vector<DevBuf*> tmp;
-  tjm::SlotDev** d_ord = nullptr;
-  tjm_status st = upload(ctx, tmp, ord.data(), ord.size(), &d_ord);
-  void* pn = nullptr;
-  if (!st) st = alloc(ctx, tmp, sizeof(int) * 4, &pn);
-  if (!st) st = launch(ctx, d_ord, (int)ord.size(), (int*)pn, max_steps, need);
+  const size_t need_bytes = ord.size() * sizeof(tjm::SlotDev*);
+  if (ctx->group_order.n < need_bytes) {
+    // grow (rare): the old list may still be read by a kernel in flight
+    TJM_CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->group_order.p) { cudaFree(ctx->group_order.p); ctx->group_order.p = nullptr; }
+    const size_t bytes = std::max(need_bytes, (size_t)4096);
+    TJM_CU(cudaMalloc(&ctx->group_order.p, bytes));
+    ctx->group_order.n = bytes;
+  }
+  if (!ctx->group_next.p) {
+    TJM_CU(cudaMalloc(&ctx->group_next.p, 16));
+    ctx->group_next.n = 16;
+  }
+  // stream-ordered refill; pageable host memory is staged before the call returns, so `ord` may go
+  TJM_CU(cudaMemcpyAsync(ctx->group_order.p, ord.data(), need_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  tjm_status st = launch(ctx, reinterpret_cast<tjm::SlotDev**>(ctx->group_order.p), (int)ord.size(),
+                         reinterpret_cast<int*>(ctx->group_next.p), max_steps, need);
   if (!st) {
     for (int i = 0; i < n_runs; ++i) {
       Run* R = find_run(ctxs[i], run_ids[i]);
@@ -740,8 +768,6 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
       if (ctxs[i] != ctx) cudaStreamWaitEvent(ctxs[i]->stream, R->done, 0);
     }
   }
-  cudaStreamSynchronize(ctx->stream);   // the temporary order array must outlive the kernel
-  for (DevBuf* b : tmp) delete b;
   return st;
 }
 

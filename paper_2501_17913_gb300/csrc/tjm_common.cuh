@@ -39,6 +39,24 @@ template <class T> __device__ __forceinline__ void cfma_cj(cx<T>& a, cx<T> b, cx
   a.x = fma(b.x, c.x, a.x); a.x = fma(b.y, c.y, a.x);
   a.y = fma(b.x, c.y, a.y); a.y = fma(-b.y, c.x, a.y);
 }
+// double-float complex arithmetic with fused real parts (tjm_df64.cuh: df_dot2, df_fma2)
+__host__ __device__ __forceinline__ cx<df64> operator*(cx<df64> a, cx<df64> b) {
+  return mk(df_dot2(a.x, b.x, -a.y, b.y), df_dot2(a.x, b.y, a.y, b.x));
+}
+__device__ __forceinline__ void cfma(cx<df64>& a, cx<df64> b, cx<df64> c) {
+  a.x = df_fma2(a.x, b.x, c.x, -b.y, c.y);
+  a.y = df_fma2(a.y, b.x, c.y, b.y, c.x);
+}
+__device__ __forceinline__ void cfma_cj(cx<df64>& a, cx<df64> b, cx<df64> c) {
+  a.x = df_fma2(a.x, b.x, c.x, b.y, c.y);
+  a.y = df_fma2(a.y, b.x, c.y, -b.y, c.x);
+}
+__host__ __device__ __forceinline__ df64 norm2(cx<df64> a) { return df_dot2(a.x, a.x, a.y, a.y); }
+// c x + s y for real c, s and complex x, y (a plane rotation's column update)
+template <class T> __device__ __forceinline__ cx<T> rot_comb(T c, cx<T> x, T s, cx<T> y) { return c * x + s * y; }
+__device__ __forceinline__ cx<df64> rot_comb(df64 c, cx<df64> x, df64 s, cx<df64> y) {
+  return mk(df_dot2(c, x.x, s, y.x), df_dot2(c, x.y, s, y.y));
+}
 template <class To, class Ti> __device__ __forceinline__ cx<To> cvt(cx<Ti> a) { return mk((To)a.x, (To)a.y); }
 template <class T> __device__ __forceinline__ cx<T> czero() { return mk((T)0, (T)0); }
 

@@ -112,6 +112,35 @@ TJM_HD df64 fabs(df64 a) { return a.hi < 0.f ? -a : a; }
 // a * b + c with the accumulation done by the sloppy adder
 TJM_HD df64 fma(df64 a, df64 b, df64 c) { return df_add_sloppy(a * b, c); }
 
+// a b + c d and acc + a b + c d with a single renormalisation: both products
+// split exactly (TwoProd on the high words), their sum and the accumulator
+// added by TwoSum, all low-order terms gathered in one FP32 word.  Error
+// bounded like the sloppy adder's (a few u^2 of |a b| + |c d| + |acc|); the
+// building block of the complex multiply-adds and Jacobi rotations below.
+TJM_HD df64 df_dot2(df64 a, df64 b, df64 c, df64 d) {
+  const float p = a.hi * b.hi, q = c.hi * d.hi;
+  const float ep = fmaf(a.hi, b.hi, -p), eq = fmaf(c.hi, d.hi, -q);
+  const df64 s = df_two_sum(p, q);
+  float t = s.lo + (ep + eq);
+  t = fmaf(a.hi, b.lo, t);
+  t = fmaf(a.lo, b.hi, t);
+  t = fmaf(c.hi, d.lo, t);
+  t = fmaf(c.lo, d.hi, t);
+  return df_fast_two_sum(s.hi, t);
+}
+TJM_HD df64 df_fma2(df64 acc, df64 a, df64 b, df64 c, df64 d) {
+  const float p = a.hi * b.hi, q = c.hi * d.hi;
+  const float ep = fmaf(a.hi, b.hi, -p), eq = fmaf(c.hi, d.hi, -q);
+  const df64 s = df_two_sum(p, q);
+  const df64 u = df_two_sum(acc.hi, s.hi);
+  float t = u.lo + s.lo + (ep + eq) + acc.lo;
+  t = fmaf(a.hi, b.lo, t);
+  t = fmaf(a.lo, b.hi, t);
+  t = fmaf(c.hi, d.lo, t);
+  t = fmaf(c.lo, d.hi, t);
+  return df_fast_two_sum(u.hi, t);
+}
+
 TJM_HD df64& operator+=(df64& x, df64 y) { x = df_add_sloppy(x, y); return x; }
 TJM_HD df64& operator-=(df64& x, df64 y) { x = df_add_sloppy(x, -y); return x; }
 TJM_HD df64& operator*=(df64& x, df64 y) { x = x * y; return x; }

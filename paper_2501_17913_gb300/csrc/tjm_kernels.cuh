@@ -154,6 +154,25 @@ __device__ bool canonicalise(const Ctx<Tc, Td>& c) {
   return true;
 }
 
+// Observables of the state m into output row `row`, then, if requested, the
+// projection error of 1TDVP at m in the row's last column.  The error sweep
+// changes the gauge, so it runs on the sampling copy (made here when m is the
+// trajectory's own state) after the observables are taken.
+template <class Tc, class Td>
+__device__ void measure_row(const Ctx<Tc, Td>& c, const Mps<Tc>& m, int row) {
+  measure(c, m, row);
+  if (!c.P->proj_err) return;
+  const Mps<Tc>* pm = &m;
+  if (m.base == c.mps.base) {
+    copy_mps(c, c.xmps, c.mps);
+    pm = &c.xmps;
+  }
+  double eps;
+  TJM_TIMED(c, PH_MEASURE, eps = projection_error(c, *pm));
+  if (threadIdx.x == 0) c.S->out[(long long)row * c.P->n_cols + c.P->n_cols - 1] = eps;
+  __syncthreads();
+}
+
 // Load the initial MPS, then canonicalise it.
 template <class Tc, class Td>
 __device__ bool init_state(const Ctx<Tc, Td>& c) {
@@ -187,7 +206,7 @@ __device__ bool finish_step(const Ctx<Tc, Td>& c, int j, bool sample) {
     double u1, u2;
     tjm_uniforms(S->seed, S->traj_id, (uint32_t)j, 0, &u1, &u2);
     TJM_TIMED(c, PH_DJ, ok = dissipate_jump(c, c.mps, P->Dfull, u1, u2));
-    if (ok && sample && P->sample_row[j] >= 0) TJM_TIMED(c, PH_MEASURE, measure(c, c.mps, P->sample_row[j]));
+    if (ok && sample && P->sample_row[j] >= 0) TJM_TIMED(c, PH_MEASURE, measure_row(c, c.mps, P->sample_row[j]));
     if (ok && j < P->n_steps) TJM_TIMED(c, PH_ENVBUILD, build_right_envs(c));
     return ok;
   }
@@ -196,7 +215,7 @@ __device__ bool finish_step(const Ctx<Tc, Td>& c, int j, bool sample) {
     double u1, u2;
     tjm_uniforms(S->seed, S->traj_id, (uint32_t)j, 1, &u1, &u2);
     TJM_TIMED(c, PH_DJ, ok = dissipate_jump(c, c.xmps, P->Dhalf, u1, u2));
-    if (ok) TJM_TIMED(c, PH_MEASURE, measure(c, c.xmps, P->sample_row[j]));
+    if (ok) TJM_TIMED(c, PH_MEASURE, measure_row(c, c.xmps, P->sample_row[j]));
   }
   if (ok && j < P->n_steps) {
     double u1, u2;
@@ -225,7 +244,7 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   if (step < 0) {
     const long long t_init = clock64();
     ok = init_state(c);
-    if (ok && P->sample_row[0] >= 0) measure(c, c.mps, P->sample_row[0]);
+    if (ok && P->sample_row[0] >= 0) measure_row(c, c.mps, P->sample_row[0]);
     if (ok && P->n_steps > 0) {
       if (P->trotter_order != 1) {      // F_0 = J(D[dt/2] .) of the Strang-split method
         double u1, u2;

@@ -307,18 +307,19 @@ __device__ __noinline__ int blk_svd_jacobi(int mm, int nn, cx<T>* a, cx<T>* u, T
         const T c = (T)1 / sqrt((T)1 + t * t), sn = c * t;
         const cx<T> ph = mk(ga.x / ag, -ga.y / ag);           // e^{-i phi}
         // [a_p, a_q] <- [a_p, a_q] [[c, sn], [-sn e^{-i phi}, c e^{-i phi}]]
+        const T msn = -sn;
         for (int r = gl, i = ia0; r < mm; r += 8) {
           const cx<T> x = ap[i], y = ph * aq[i];
-          ap[i] = c * x - sn * y;
-          aq[i] = sn * x + c * y;
+          ap[i] = rot_comb(c, x, msn, y);
+          aq[i] = rot_comb(sn, x, c, y);
           i += 8; if (i >= mm) i -= mm;
         }
         cx<T>* vp = vw + (long long)p * nn;
         cx<T>* vq = vw + (long long)qq * nn;
         for (int r = gl, i = iv0; r < nn; r += 8) {
           const cx<T> x = vp[i], y = ph * vq[i];
-          vp[i] = c * x - sn * y;
-          vq[i] = sn * x + c * y;
+          vp[i] = rot_comb(c, x, msn, y);
+          vq[i] = rot_comb(sn, x, c, y);
           i += 8; if (i >= nn) i -= nn;
         }
         if (gl == 0) atomicAdd(&rot_count, 1);

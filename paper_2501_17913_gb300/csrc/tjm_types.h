@@ -34,6 +34,8 @@ struct ProbDev {
   const cx<double>* oop2;                 // [n_obs2][16], row (t1 t2), column (s1 s2)
   const int* site_has2;                   // [L]: 1 if some two-site observable starts at the site
   int trotter_order;                      // 2: the Strang-split TJM; 1: the first-order baseline
+  int proj_err;                           // 1: the last output column is the 1TDVP projection error
+  int n_cols;                             // output columns: n_obs + n_obs2 + proj_err
 };
 
 struct SlotStats {

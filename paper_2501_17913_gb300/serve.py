@@ -26,7 +26,8 @@ from . import tjm
 
 
 def state_bytes(wl, precision) -> int:
-    """Device bytes of a request's trajectory state (sites, environments, outputs)."""
+    """Device bytes of a request's trajectory state (sites, environments, outputs); the per-CTA scratch
+    the batched launches hold is accounted for separately (Server._scratch_need)."""
     szc = 16 if precision == tjm.PREC_FP64 else 8
     chi = wl.chi_max
     D = max(int(np.shape(w)[1]) for w in wl.W)
@@ -53,7 +54,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, precision=tjm.PREC_FP32_DEC32, mem_budget=None, steps_per_tick=1, device=0,
+    def __init__(self, precision=tjm.PREC_FP32_DF64, mem_budget=None, steps_per_tick=1, device=0,
                  keep_per_traj=False, tuner=None, backend=tjm, clock=time.perf_counter):
         # backend: the library binding (tjm); a stand-in with the same names lets the host logic
         # run without a GPU
@@ -91,13 +92,21 @@ class Server:
         self.queue.append(r)
         return r.rid
 
+    def _scratch_need(self, extra=None):
+        """Bytes of the launch scratch for the largest (chi_max, L) among the active requests (and `extra`):
+        every resident CTA holds one trajectory's scratch, sized by the largest request in the launch."""
+        wls = [r.wl for r in self.active] + ([extra] if extra is not None else [])
+        if not wls or not hasattr(self.anchor, "scratch_bytes"):
+            return 0
+        return self.anchor.scratch_bytes(max(w.chi_max for w in wls), max(w.L for w in wls))
+
     def _admit(self, now):
         still = []
         for r in self.queue:
             if r.arrival > now:
                 still.append(r)
                 continue
-            if self.used + r.bytes > self.budget and self.active:
+            if self.used + r.bytes + self._scratch_need(r.wl) > self.budget and self.active:
                 still.append(r)          # wait for memory; admit in arrival order
                 continue
             wl = r.wl
@@ -119,11 +128,17 @@ class Server:
         if not self.active:
             return bool(self.queue)
         pairs = [(self.anchor, self.anchor_run)] + [(r.ctx, r.run) for r in self.active]
-        self.tj.group_advance(pairs, self.steps)
+        self.tj.group_advance(pairs, self.steps)      # asynchronous
         self.launches += 1
+        # requests that arrive while the launch runs are prepared now and join the next launch
+        self._admit(self.clock())
         self.anchor.sync()
         still = []
+        launched = {id(c) for (c, _) in pairs}
         for r in self.active:
+            if id(r.ctx) not in launched:
+                still.append(r)          # admitted during the launch
+                continue
             st = r.ctx.stats(r.run)
             if st['steps_done_min'] >= r.wl.n_steps or st['failed'] == st['n_traj']:
                 r.mean, r.sem, pt = r.ctx.result(r.run, per_traj=self.keep, allow_numeric=True)

@@ -45,7 +45,7 @@ class tjm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int),
                 ("energy_shift", C.c_int), ("tile_rule", C.c_int), ("tensor_cores", C.c_int),
-                ("trotter_order", C.c_int)]
+                ("trotter_order", C.c_int), ("projection_error", C.c_int)]
 
 
 class tjm_stats(C.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = [
     ("tjm_run_advance", C.c_int, [C.c_void_p, C.c_int64, C.c_int]),
     ("tjm_run_group_advance", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int, C.c_int]),
     ("tjm_poll", C.c_int, [C.c_void_p, C.c_int64]),
+    ("tjm_scratch_bytes", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
     ("tjm_result", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.POINTER(C.c_double)]),
     ("tjm_run_stats", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(tjm_stats)]),
@@ -165,7 +166,7 @@ class Context:
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32_DF64, krylov_max=30, krylov_tol=0.0,
                  exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0, tensor_cores=True,
-                 trotter_order=2):
+                 trotter_order=2, projection_error=False):
         lib = load()
         self.lib = lib
         L = len(W)
@@ -186,6 +187,8 @@ class Context:
         opt.tile_rule = int(tile_rule)
         opt.tensor_cores = int(bool(tensor_cores))
         opt.trotter_order = int(trotter_order)
+        opt.projection_error = int(bool(projection_error))
+        self.projection_error = bool(projection_error)
         h = C.c_void_p()
         st = lib.tjm_create(C.byref(h), C.byref(mpo), js, len(jumps), float(dt), int(chi_max), float(trunc_eps),
                             C.byref(opt))
@@ -247,8 +250,10 @@ class Context:
         self._check(st, "tjm_run" if launch else "tjm_run_prepare")
         # device column of each caller observable: the one-site ones first, then the two-site ones
         order = [i for (i, _, _) in one] + [i for (i, _, _) in two]
+        if self.projection_error:
+            order.append(len(observables))        # the projection error stays the last column
         inv = np.argsort(order) if order else np.zeros(0, dtype=int)
-        self.runs[rid.value] = (int(n_traj), len(t), len(observables), inv)
+        self.runs[rid.value] = (int(n_traj), len(t), len(order), inv)
         return rid.value
 
     def run(self, psi0, n_traj, seed, observables, times, first_traj=0):
@@ -338,6 +343,12 @@ class Context:
     def free(self, run_id):
         self._check(self.lib.tjm_run_free(self.h, run_id), "tjm_run_free")
         self.runs.pop(run_id, None)
+
+    def scratch_bytes(self, chi_cap, L):
+        """Device bytes of the per-CTA scratch a launch holds for trajectories up to (chi_cap, L)."""
+        out = C.c_int64()
+        self._check(self.lib.tjm_scratch_bytes(self.h, int(chi_cap), int(L), C.byref(out)), "tjm_scratch_bytes")
+        return int(out.value)
 
     def sync(self):
         self._check(self.lib.tjm_sync(self.h), "tjm_sync")

@@ -1,7 +1,8 @@
 // Host driver for the double-float arithmetic of the GPU factorizations
 // (csrc/tjm_df64.cuh compiled as plain C++): reads lines "a_hi a_lo b_hi b_lo
 // c_hi c_lo" of hexadecimal floats and prints, as hexadecimal floats, the
-// (hi, lo) words of a+b, a-b, a*b, a/b, sqrt(|a|), fma(a, b, c).
+// (hi, lo) words of a+b, a-b, a*b, a/b, sqrt(|a|), fma(a, b, c), a*b + c*a and
+// c + a*b + b*c.
 #include <cstdio>
 
 #include "tjm_df64.cuh"
@@ -20,6 +21,8 @@ int main() {
     out(a / b);
     out(sqrt(tjm::fabs(a)));
     out(fma(a, b, c));
+    out(tjm::df_dot2(a, b, c, a));
+    out(tjm::df_fma2(c, a, b, b, c));
     std::printf("\n");
   }
   return 0;

@@ -64,7 +64,7 @@ def test_df64_operations_match_exact_arithmetic():
     u2 = Fraction(1, 2 ** 48)
     for i in range(n):
         w = [float.fromhex(t) for t in res[i].split()]
-        got = [_fr(w[2 * k], w[2 * k + 1]) for k in range(6)]
+        got = [_fr(w[2 * k], w[2 * k + 1]) for k in range(8)]
         A, B, Cc = _fr(a[0][i], a[1][i]), _fr(b[0][i], b[1][i]), _fr(c[0][i], c[1][i])
         exact = [A + B, A - B, A * B, A / B]
         for k, e in enumerate(exact):
@@ -74,8 +74,13 @@ def test_df64_operations_match_exact_arithmetic():
         # fma with the sloppy adder: error bounded by the summands' magnitudes
         e = A * B + Cc
         assert abs(got[5] - e) <= 16 * u2 * (abs(A * B) + abs(Cc)), (i, "fma")
+        # the fused two-product forms: error bounded by the magnitudes of their terms
+        e = A * B + Cc * A
+        assert abs(got[6] - e) <= 16 * u2 * (abs(A * B) + abs(Cc * A)), (i, "dot2")
+        e = Cc + A * B + B * Cc
+        assert abs(got[7] - e) <= 16 * u2 * (abs(Cc) + abs(A * B) + abs(B * Cc)), (i, "fma2")
         # every result is normalised: |lo| <= ulp(hi) / 2
-        for k in range(6):
+        for k in range(8):
             hi, lo = w[2 * k], w[2 * k + 1]
             if hi != 0.0:
                 assert abs(lo) <= np.spacing(np.float32(abs(hi))) / 2 * 1.0000001, (i, k, hi, lo)

@@ -141,20 +141,25 @@ def test_bench_workload_one_step(prec, tol):
 
 
 def test_uneven_batch_one_launch_matches_alone_and_oracle():
-    """4096 trajectories over 32 groups (L in {50,100,200}, chi_max in {16,32,64}, gamma in {0.01,0.1,1}),
-    all in one persistent launch, 3 steps: every group's results equal the same group run alone, and
-    sampled trajectories match the oracle."""
+    """The uneven batch: all 32 groups (L in {50,100,200}, chi_max in {16,32,64}, gamma in {0.01,0.1,1},
+    g ~ U[0,1], Haar-random product states from seed 7, dt = 0.05) for the full 100 steps (T = 5) in ONE
+    persistent launch, PER_GROUP trajectories per group (the full 128 per group is 48 M trajectory*site*
+    steps, hours of GPU time).  Every group's trajectories equal, bit for bit, the same trajectories
+    run in a launch of their own (all 32 single-group launches in flight at once on their own streams),
+    and one trajectory of every group matches the oracle over the first 3 steps."""
     from _pool import oracle_pool
     from oracle_jobs import run_traj
     lib_ready()
+    PER_GROUP = 4
     groups = I.uneven_groups()
-    n_steps = 3
+    n_steps = groups[0].n_steps
+    assert n_steps == 100
+    samples = [0, 1, 2, 3, 50, n_steps]
     ctxs, runs = [], []
     for wl in groups:
-        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DEC32)
-        times = [s * wl.dt for s in range(n_steps + 1)]
-        r = ctx.prepare(np.array(wl.psi0_per_traj), wl.n_traj, wl.seed, wl.observables, times,
-                        first_traj=wl.meta['first_traj'])
+        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DF64)
+        r = ctx.prepare(np.array(wl.psi0_per_traj[:PER_GROUP]), PER_GROUP, wl.seed, wl.observables,
+                        [s * wl.dt for s in samples], first_traj=wl.meta['first_traj'])
         ctxs.append(ctx)
         runs.append(r)
     tjm.group_advance(list(zip(ctxs, runs)), n_steps + 1)
@@ -163,26 +168,31 @@ def test_uneven_batch_one_launch_matches_alone_and_oracle():
         pt = ctx.result(r)[2]
         st = ctx.stats(r)
         _check_properties(pt, st, wl.chi_max)
+        assert st['steps_done_min'] == n_steps
         mixed.append(pt)
-    # alone: two groups with different L and chi, each in its own launch
-    for gi in (0, 31):
-        wl = groups[gi]
-        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DEC32)
-        times = [s * wl.dt for s in range(n_steps + 1)]
-        r = ctx.run(np.array(wl.psi0_per_traj), wl.n_traj, wl.seed, wl.observables, times,
+    # alone: each group in its own launch, all launched before any result is read
+    alone_ctx, alone_run = [], []
+    for wl in groups:
+        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DF64)
+        r = ctx.run(np.array(wl.psi0_per_traj[:2]), 2, wl.seed, wl.observables, [s * wl.dt for s in samples],
                     first_traj=wl.meta['first_traj'])
+        alone_ctx.append(ctx)
+        alone_run.append(r)
+    for gi, (ctx, r) in enumerate(zip(alone_ctx, alone_run)):
         alone = ctx.result(r)[2]
-        assert np.array_equal(alone, mixed[gi]), gi
+        assert np.array_equal(alone, mixed[gi][:2]), gi
         ctx.close()
-    # oracle: one trajectory of each of a few groups (cheap: short times, product start)
-    picks = [(0, 5), (13, 77), (26, 127)]
-    with oracle_pool(len(picks)) as pool:
-        res = pool.map(run_traj, [('uneven_group', {'gi': gi, 'n_steps': n_steps}, k, {'n_steps': n_steps,
-                                                                   'traj_offset': groups[gi].meta['first_traj']})
-                                  for gi, k in picks])
-    for (gi, k), (v, stt) in zip(picks, res):
+    # oracle: trajectory 0 of every group over the first 3 steps (product start: cheap)
+    jobs = [('uneven_group', {'gi': gi, 'n_steps': 3}, 0, {'n_steps': 3, 'traj_offset': groups[gi].meta['first_traj']})
+            for gi in range(len(groups))]
+    with oracle_pool() as pool:
+        res = pool.map(run_traj, jobs)
+    checked = 0
+    for gi, (v, stt) in enumerate(res):
         if min(stt['min_margin1'], stt['min_margin2']) < 1e-5:
             continue
-        assert np.abs(mixed[gi][k] - v).max() < 1e-4, (gi, k)
+        assert np.abs(mixed[gi][0][:4] - v).max() < 1e-4, (gi, np.abs(mixed[gi][0][:4] - v).max())
+        checked += 1
+    assert checked >= len(groups) - 4, checked
     for ctx in ctxs:
         ctx.close()
