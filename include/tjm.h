@@ -60,7 +60,7 @@ enum {
  *               significand) on the FP32 pipes.  GB300 executes 2 native FP64
  *               FMAs per clock per SM against 128 FP32 FMAs; the emulation
  *               gives the FP64 factorizations about 3x the native rate with
- *               results equal to native FP64 to ~1e-13. */
+ *               results equal to native FP64 to ~1e-11 relative. */
 enum { TJM_PREC_FP64 = 0, TJM_PREC_FP32 = 1, TJM_PREC_FP32_DEC32 = 2, TJM_PREC_FP32_DF64 = 3 };
 
 /* Hamiltonian H0 as a matrix product operator (Methods, Sec. "Matrix product

@@ -67,6 +67,7 @@ class TileAutotuner:
         return rule
 
     def report(self):
-        return {"%s/chi%d" % (("fp64", "fp32d64", "fp32")[k[0]], k[1]):
+        names = {0: "f64", 1: "f32+f64", 2: "f32", 3: "f32+df64"}
+        return {"%s/chi%d" % (names.get(k[0], str(k[0])), k[1]):
                 {"best": self.best.get(k), "rates_tflops": {r: v / 1e12 for r, v in t.items()}}
                 for k, t in self.trials.items()}

@@ -219,11 +219,12 @@ void pad_product(int L, const std::vector<zc>& phi, std::vector<zc>& data, std::
 
 int resident(tjm_ctx* ctx) {
   int per_sm = 0, sms = 0;
+  const int tc = ctx->opt.tensor_cores;
   switch (ctx->opt.precision) {
-    case TJM_PREC_FP64: per_sm = tjm::occupancy_f64(); break;
-    case TJM_PREC_FP32_DEC32: per_sm = tjm::occupancy_f32d32(); break;
-    case TJM_PREC_FP32_DF64: per_sm = tjm::occupancy_f32df(); break;
-    default: per_sm = tjm::occupancy_f32(); break;
+    case TJM_PREC_FP64: per_sm = tjm::occupancy_f64(tc); break;
+    case TJM_PREC_FP32_DEC32: per_sm = tjm::occupancy_f32d32(tc); break;
+    case TJM_PREC_FP32_DF64: per_sm = tjm::occupancy_f32df(tc); break;
+    default: per_sm = tjm::occupancy_f32(tc); break;
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   return std::max(1, per_sm) * std::max(1, sms);

@@ -6,18 +6,21 @@
 namespace tjm {
 
 cudaError_t launch_f32(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                      char* scratch, long long stride, ScratchDims dims, int use_tc) {
+                        char* scratch, long long stride, ScratchDims dims, int use_tc) {
   auto kern = advance_kernel<float, double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, double>());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, double>(true));
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<float, double>(), s>>>(order, n, next, max_steps, scratch, stride, dims, use_tc);
+  kern<<<ctas, TJM_THREADS, smem_bytes<float, double>(use_tc != 0), s>>>(order, n, next, max_steps, scratch, stride, dims,
+                                                                  use_tc);
   return cudaGetLastError();
 }
 
-int occupancy_f32() {
+int occupancy_f32(int use_tc) {
   int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, double>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, double>, TJM_THREADS, smem_bytes<float, double>());
+  cudaFuncSetAttribute(advance_kernel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_bytes<float, double>(true));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, double>, TJM_THREADS,
+                                                smem_bytes<float, double>(use_tc != 0));
   return per_sm;
 }
 

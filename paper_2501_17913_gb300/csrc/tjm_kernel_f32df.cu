@@ -6,18 +6,21 @@
 namespace tjm {
 
 cudaError_t launch_f32df(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                         char* scratch, long long stride, ScratchDims dims, int use_tc) {
+                        char* scratch, long long stride, ScratchDims dims, int use_tc) {
   auto kern = advance_kernel<float, df64>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, df64>());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, df64>(true));
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<float, df64>(), s>>>(order, n, next, max_steps, scratch, stride, dims, use_tc);
+  kern<<<ctas, TJM_THREADS, smem_bytes<float, df64>(use_tc != 0), s>>>(order, n, next, max_steps, scratch, stride, dims,
+                                                                  use_tc);
   return cudaGetLastError();
 }
 
-int occupancy_f32df() {
+int occupancy_f32df(int use_tc) {
   int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<float, df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, df64>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, df64>, TJM_THREADS, smem_bytes<float, df64>());
+  cudaFuncSetAttribute(advance_kernel<float, df64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_bytes<float, df64>(true));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, df64>, TJM_THREADS,
+                                                smem_bytes<float, df64>(use_tc != 0));
   return per_sm;
 }
 

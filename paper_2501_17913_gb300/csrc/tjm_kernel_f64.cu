@@ -6,18 +6,21 @@
 namespace tjm {
 
 cudaError_t launch_f64(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                      char* scratch, long long stride, ScratchDims dims, int use_tc) {
+                        char* scratch, long long stride, ScratchDims dims, int use_tc) {
   auto kern = advance_kernel<double, double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double, double>());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double, double>(true));
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<double, double>(), s>>>(order, n, next, max_steps, scratch, stride, dims, use_tc);
+  kern<<<ctas, TJM_THREADS, smem_bytes<double, double>(use_tc != 0), s>>>(order, n, next, max_steps, scratch, stride, dims,
+                                                                  use_tc);
   return cudaGetLastError();
 }
 
-int occupancy_f64() {
+int occupancy_f64(int use_tc) {
   int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double, double>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<double, double>, TJM_THREADS, smem_bytes<double, double>());
+  cudaFuncSetAttribute(advance_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem_bytes<double, double>(true));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<double, double>, TJM_THREADS,
+                                                smem_bytes<double, double>(use_tc != 0));
   return per_sm;
 }
 

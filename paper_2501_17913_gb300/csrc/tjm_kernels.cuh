@@ -74,7 +74,12 @@ constexpr int kSmemFsmOff = kSmemGsmOff + kSmemGemm;
 constexpr int kFsmBytes = 65536;
 constexpr int kSmemFsvOff = kSmemFsmOff + kFsmBytes;
 static_assert(kSmemFsvOff - kSmemGsmOff >= tc::kSmemBytes, "tensor-core stages fit the GEMM and factorization areas");
-template <class Tc, class Td> constexpr int smem_bytes() { return sizeof(Tc) == 4 ? kSmemFsvOff + 1024 : kSmemFsmOff; }
+// Dynamic shared memory of a launch: the 96 KB tensor-core / FP32-factorization area only when it
+// is used, so that an FP64 / double-float factorization launch on the CUDA cores leaves the rest
+// of the SM's L1 to cache its global workspace.
+template <class Tc, class Td> constexpr int smem_bytes(bool use_tc) {
+  return (sizeof(Tc) == 4 && (use_tc || sizeof(Td) == 4)) ? kSmemFsvOff + 1024 : kSmemFsmOff;
+}
 
 template <class Tc, class Td>
 __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDims& dims, char* smem) {

@@ -137,12 +137,12 @@ extern "C" tjm_status tjm_selftest_contract(int kind, int precision, int tensor_
     return TJM_ENOMEM;
   cudaError_t e;
   if (precision == TJM_PREC_FP64) {
-    const int sm = tjm::smem_bytes<double, double>();
+    const int sm = tjm::smem_bytes<double, double>(false);
     auto k = tjm::contract_test_kernel<double, double>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     k<<<1, TJM_THREADS, sm>>>(kind, dS, scr, dims, dLin, nL, lb, dRin, nR, rb, dx, nx, dy, ny, chl, chr, 0);
   } else {
-    const int sm = tjm::smem_bytes<float, double>();
+    const int sm = tjm::smem_bytes<float, double>(true);
     auto k = tjm::contract_test_kernel<float, double>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     k<<<1, TJM_THREADS, sm>>>(kind, dS, scr, dims, dLin, nL, lb, dRin, nR, rb, dx, nx, dy, ny, chl, chr,

@@ -5,24 +5,25 @@
 // The effective-Hamiltonian and environment contractions of the TDVP sweep
 // (paper Fig. 2: L . W . A . R) are complex GEMMs whose operands are FP32.
 // They run here as real GEMMs on the tensor pipe:
-//   * complex -> real ("4M" split in one product): the interleaved complex A
-//     (M x K) is the real matrix [a_re a_im ...] of M x 2K; B is expanded to
-//     the real 2K x 2N matrix of 2x2 blocks [[b_re, b_im], [-b_im, b_re]], so
-//     the real product is C interleaved (M x 2N);
+//   * complex -> real ("4M" in planar form): A and B are staged as separate
+//     real and imaginary planes, and the two accumulators of tensor memory
+//     receive C_re = A_re B_re - A_im B_im (the second product with the MMA's
+//     negate-A bit) and C_im = A_re B_im + A_im B_re;
 //   * FP32 accuracy from TF32 inputs ("3xTF32"): x = hi + lo with hi = x
 //     rounded to TF32 and lo the FP32 remainder, and A B = Ahi Bhi + Ahi Blo +
 //     Alo Bhi up to the dropped Alo Blo (2^-22 relative) -- three MMAs per
-//     k-step accumulating in FP32 in tensor memory.
-// One thread issues tcgen05.mma (kind::tf32, M = 128, N <= 256, K = 8) from
+//     real product, twelve per k-step, accumulating in FP32 in tensor memory.
+// One thread issues tcgen05.mma (kind::tf32, M = 128, N <= 128, K = 8) from
 // shared-memory operand tiles in the K-major no-swizzle core-matrix layout;
-// the accumulator (128 lanes x N FP32 columns) lives in tensor memory and is
-// read back with tcgen05.ld.  Operand tiles pass through registers on their
-// way to shared memory because every element is split (hi / lo) and B is
-// expanded, which a bulk tensor copy cannot do; two stages let the loads of
-// one K chunk overlap the MMAs of the previous one, ordered by mbarriers that
-// tcgen05.commit arrives on.  Every mbarrier wait is bounded: on timeout the
-// CTA records the failure, stops issuing MMAs and the caller marks the
-// trajectory failed.
+// the accumulators (128 lanes x 2N FP32 columns) live in tensor memory and
+// are read back with tcgen05.ld.  Operand tiles pass through registers on
+// their way to shared memory because every element is split (hi / lo) and
+// de-interleaved, which a bulk tensor copy cannot do; the global loads of the
+// next K chunk are issued before the current one is written, and three
+// stages let the loads of one chunk overlap the MMAs of the previous ones,
+// ordered by mbarriers that tcgen05.commit arrives on.  Every mbarrier wait
+// is bounded: on timeout the CTA records the failure, stops issuing MMAs and
+// the caller marks the trajectory failed.
 #pragma once
 #include <stdint.h>
 
@@ -33,23 +34,22 @@ namespace tc {
 
 // ------------------------------------------------------------------ geometry
 constexpr int kM = 128;                         // MMA rows (TMEM lanes)
-constexpr int kNr = 256;                        // max real columns per tile (TMEM columns)
-constexpr int kKc = 8;                          // complex K per stage
-constexpr int kKr = 2 * kKc;                    // real K per stage (two MMAs of K = 8)
-constexpr int kKq = kKr / 4;                    // core matrices (4 TF32 wide) along K per stage
-constexpr int kABytes = kM * kKr * 4;           // one A tile (hi or lo)
-constexpr int kBBytes = kNr * kKr * 4;          // one B tile (hi or lo)
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kStages = 2;
+constexpr int kNc = 128;                        // max complex columns per tile (re + im: 256 TMEM columns)
+constexpr int kKc = 8;                          // complex K per stage: one MMA k-step of 8 TF32
+constexpr int kKq = kKc / 4;                    // core matrices (4 TF32 wide) along K per stage
+constexpr int kPlaneA = kM * kKc * 4;           // one A plane (re or im, hi or lo)
+constexpr int kPlaneB = kNc * kKc * 4;          // one B plane
+constexpr int kStageBytes = 4 * kPlaneA + 4 * kPlaneB;
+constexpr int kStages = 3;
 constexpr int kSmemBytes = kStages * kStageBytes;   // 96 KB of operand staging
 constexpr int kTmemCols = 256;
 
-// Byte offset of real element (row, kr) in a K-major, no-swizzle operand tile:
+// Byte offset of real element (row, k) in a K-major, no-swizzle operand plane:
 // 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart (the
 // descriptor's leading-dimension offset), 8-row groups kKq * 128 B apart (its
 // stride-dimension offset).
-__device__ __forceinline__ int core_off(int row, int kr) {
-  return ((((row >> 3) * kKq) + (kr >> 2)) << 7) + ((row & 7) << 4) + ((kr & 3) << 2);
+__device__ __forceinline__ int core_off(int row, int k) {
+  return ((((row >> 3) * kKq) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
 }
 constexpr uint32_t kLBO = 128;
 constexpr uint32_t kSBO = kKq * 128;
@@ -106,10 +106,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return d;
 }
 // Instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28, dense, no negation.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// (bits 7-9, 10-12 = 2), negate A (bit 13), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28, dense.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool neg_a = false) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -231,102 +232,119 @@ __device__ __forceinline__ cx<float> tc_loadB(const TcB& b, int K, int N, int k,
 // threads of the CTA call it; smem is the 96 KB staging area (16-byte
 // aligned).  Returns false if a wait timed out (results are then undefined).
 static __device__ __noinline__ bool cgemm(Ctl* ctl, int M, int N, int K, cx<float> alpha, TcA A, TcB B, cx<float>* C,
-                                   long long sci, long long scj, bool accumulate, char* smem) {
+                                          long long sci, long long scj, bool accumulate, char* smem) {
   if (ctl->failed) return false;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const bool a_kc = A.fused || A.sk == 1 || A.si != 1;     // A's k index is the contiguous one
-  const bool b_nc = B.sj == 1 || B.sk != 1;                 // B's j index is the contiguous one
+  const bool b_kc = !(B.sj == 1 || B.sk != 1);              // B's k index is the contiguous one
+  // each thread stages one row of A and one row of B, 4 consecutive k of the 8 in a chunk
+  const int ra = a_kc ? (tid >> 1) : (tid & 127), qa = a_kc ? (tid & 1) : (tid >> 7);
+  const int rb = b_kc ? (tid >> 1) : (tid & 127), qb = b_kc ? (tid & 1) : (tid >> 7);
   const int nk = (K + kKc - 1) / kKc;
-  const int ntile_n = (N + kNr / 2 - 1) / (kNr / 2);
+  const int ntile_n = (N + kNc - 1) / kNc;
   const uint32_t sbase = saddr(smem);
   for (int i0 = 0; i0 < M; i0 += kM) {
     for (int tn = 0; tn < ntile_n; ++tn) {
-      const int j0 = tn * (kNr / 2);
-      const int nt = N - j0 < kNr / 2 ? N - j0 : kNr / 2;     // complex columns of this tile
-      const int ntp = (nt + 7) & ~7;                             // padded to the MMA's N granularity
-      const uint32_t idesc = idesc_tf32(kM, 2 * ntp);
-      for (int kc = 0; kc < nk; ++kc) {
+      const int j0 = tn * kNc;
+      const int nt = N - j0 < kNc ? N - j0 : kNc;      // complex columns of this tile
+      const int ntp = (nt + 15) & ~15;                   // padded to the M = 128 MMA's N granularity
+      const uint32_t idesc = idesc_tf32(kM, ntp), idesc_neg = idesc_tf32(kM, ntp, true);
+      const uint32_t t_re = ctl->tmem, t_im = ctl->tmem + (uint32_t)ntp;
+      cx<float> xa[4], xb[4];
+      auto fetch = [&](int kc) {
         const int k0 = kc * kKc;
-        const int st = kc & 1;
-        // global -> registers first, so the loads are in flight while we wait for the stage
-        cx<float> ra[4], rb[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int ia = a_kc ? (tid >> 1) : ((tid & 31) * 4 + q);
-          const int ka = a_kc ? ((tid & 1) * 4 + q) : (tid >> 5);
-          ra[q] = tc_loadA(A, M, K, i0 + ia, k0 + ka);
-          const int kb = b_nc ? (tid >> 5) : ((tid & 1) * 4 + q);
-          const int jb = b_nc ? ((tid & 31) * 4 + q) : (tid >> 1);
-          rb[q] = jb < ntp ? tc_loadB(B, K, N, k0 + kb, j0 + jb) : czero<float>();
+          xa[q] = tc_loadA(A, M, K, i0 + ra, k0 + 4 * qa + q);
+          xb[q] = rb < ntp ? tc_loadB(B, K, N, k0 + 4 * qb + q, j0 + rb) : czero<float>();
         }
-        if (kc >= kStages && !stage_wait(ctl, st)) return false;
-        char* sA = smem + st * kStageBytes;
-        char* sAl = sA + kABytes;
-        char* sB = sAl + kABytes;
-        char* sBl = sB + kBBytes;
+      };
+      fetch(0);
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % kStages;
+        cx<float> ca[4], cb[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int ia = a_kc ? (tid >> 1) : ((tid & 31) * 4 + q);
-          const int ka = a_kc ? ((tid & 1) * 4 + q) : (tid >> 5);
-          float2 h, l;
-          split_tf32(ra[q].x, h.x, l.x);
-          split_tf32(ra[q].y, h.y, l.y);
-          const int oa = core_off(ia, 2 * ka);
-          *reinterpret_cast<float2*>(sA + oa) = h;
-          *reinterpret_cast<float2*>(sAl + oa) = l;
-          const int kb = b_nc ? (tid >> 5) : ((tid & 1) * 4 + q);
-          const int jb = b_nc ? ((tid & 31) * 4 + q) : (tid >> 1);
-          if (jb < ntp) {
-            float brh, brl, bih, bil;
-            split_tf32(rb[q].x, brh, brl);
-            split_tf32(rb[q].y, bih, bil);
-            // rows 2j (real part of C) and 2j+1 (imaginary part), columns 2k (times a_re), 2k+1 (times a_im)
-            const int o0 = core_off(2 * jb, 2 * kb), o1 = core_off(2 * jb + 1, 2 * kb);
-            *reinterpret_cast<float2*>(sB + o0) = make_float2(brh, -bih);
-            *reinterpret_cast<float2*>(sB + o1) = make_float2(bih, brh);
-            *reinterpret_cast<float2*>(sBl + o0) = make_float2(brl, -bil);
-            *reinterpret_cast<float2*>(sBl + o1) = make_float2(bil, brl);
-          }
+        for (int q = 0; q < 4; ++q) { ca[q] = xa[q]; cb[q] = xb[q]; }
+        if (kc + 1 < nk) fetch(kc + 1);        // in flight while this chunk is split and written
+        if (kc >= kStages && !stage_wait(ctl, st)) return false;
+        char* sp = smem + st * kStageBytes;
+        {
+          float4 rh, rl, ih, il;
+          split_tf32(ca[0].x, rh.x, rl.x); split_tf32(ca[1].x, rh.y, rl.y);
+          split_tf32(ca[2].x, rh.z, rl.z); split_tf32(ca[3].x, rh.w, rl.w);
+          split_tf32(ca[0].y, ih.x, il.x); split_tf32(ca[1].y, ih.y, il.y);
+          split_tf32(ca[2].y, ih.z, il.z); split_tf32(ca[3].y, ih.w, il.w);
+          const int o = core_off(ra, 4 * qa);
+          *reinterpret_cast<float4*>(sp + o) = rh;
+          *reinterpret_cast<float4*>(sp + kPlaneA + o) = rl;
+          *reinterpret_cast<float4*>(sp + 2 * kPlaneA + o) = ih;
+          *reinterpret_cast<float4*>(sp + 3 * kPlaneA + o) = il;
+        }
+        if (rb < ntp) {
+          float4 rh, rl, ih, il;
+          split_tf32(cb[0].x, rh.x, rl.x); split_tf32(cb[1].x, rh.y, rl.y);
+          split_tf32(cb[2].x, rh.z, rl.z); split_tf32(cb[3].x, rh.w, rl.w);
+          split_tf32(cb[0].y, ih.x, il.x); split_tf32(cb[1].y, ih.y, il.y);
+          split_tf32(cb[2].y, ih.z, il.z); split_tf32(cb[3].y, ih.w, il.w);
+          const int o = core_off(rb, 4 * qb);
+          char* sb = sp + 4 * kPlaneA;
+          *reinterpret_cast<float4*>(sb + o) = rh;
+          *reinterpret_cast<float4*>(sb + kPlaneB + o) = rl;
+          *reinterpret_cast<float4*>(sb + 2 * kPlaneB + o) = ih;
+          *reinterpret_cast<float4*>(sb + 3 * kPlaneB + o) = il;
         }
         fence_proxy_async();
         fence_before_sync();
         __syncthreads();
         if (tid == 0) {
           fence_after_sync();
-          const uint32_t a_hi = sbase + st * kStageBytes, a_lo = a_hi + kABytes;
-          const uint32_t b_hi = a_lo + kABytes, b_lo = b_hi + kBBytes;
-#pragma unroll
-          for (int s = 0; s < kKr / 8; ++s) {
-            const uint32_t ko = s * 2 * 128;     // two core matrices (8 TF32) per MMA k-step
-            const uint32_t acc0 = (kc > 0 || s > 0) ? 1u : 0u;
-            mma_tf32(ctl->tmem, sdesc(a_lo + ko, kLBO, kSBO), sdesc(b_hi + ko, kLBO, kSBO), idesc, acc0);
-            mma_tf32(ctl->tmem, sdesc(a_hi + ko, kLBO, kSBO), sdesc(b_lo + ko, kLBO, kSBO), idesc, 1u);
-            mma_tf32(ctl->tmem, sdesc(a_hi + ko, kLBO, kSBO), sdesc(b_hi + ko, kLBO, kSBO), idesc, 1u);
-          }
+          const uint32_t a0 = sbase + st * kStageBytes;
+          const uint64_t are_h = sdesc(a0, kLBO, kSBO), are_l = sdesc(a0 + kPlaneA, kLBO, kSBO);
+          const uint64_t aim_h = sdesc(a0 + 2 * kPlaneA, kLBO, kSBO), aim_l = sdesc(a0 + 3 * kPlaneA, kLBO, kSBO);
+          const uint32_t b0 = a0 + 4 * kPlaneA;
+          const uint64_t bre_h = sdesc(b0, kLBO, kSBO), bre_l = sdesc(b0 + kPlaneB, kLBO, kSBO);
+          const uint64_t bim_h = sdesc(b0 + 2 * kPlaneB, kLBO, kSBO), bim_l = sdesc(b0 + 3 * kPlaneB, kLBO, kSBO);
+          const uint32_t acc0 = kc > 0 ? 1u : 0u;
+          // C_re += A_re B_re - A_im B_im   (small terms first)
+          mma_tf32(t_re, are_l, bre_h, idesc, acc0);
+          mma_tf32(t_re, are_h, bre_l, idesc, 1u);
+          mma_tf32(t_re, are_h, bre_h, idesc, 1u);
+          mma_tf32(t_re, aim_l, bim_h, idesc_neg, 1u);
+          mma_tf32(t_re, aim_h, bim_l, idesc_neg, 1u);
+          mma_tf32(t_re, aim_h, bim_h, idesc_neg, 1u);
+          // C_im += A_re B_im + A_im B_re
+          mma_tf32(t_im, are_l, bim_h, idesc, acc0);
+          mma_tf32(t_im, are_h, bim_l, idesc, 1u);
+          mma_tf32(t_im, are_h, bim_h, idesc, 1u);
+          mma_tf32(t_im, aim_l, bre_h, idesc, 1u);
+          mma_tf32(t_im, aim_h, bre_l, idesc, 1u);
+          mma_tf32(t_im, aim_h, bre_h, idesc, 1u);
           mma_commit(&ctl->bar[st]);
           ctl->issued[st] += 1;
         }
         __syncthreads();
       }
       // drain: every commit of this tile completed (they complete in order)
-      for (int s = 0; s < kStages; ++s)
-        while (ctl->waited[s] < ctl->issued[s])
-          if (!stage_wait(ctl, s)) return false;
+      for (int s2 = 0; s2 < kStages; ++s2)
+        while (ctl->waited[s2] < ctl->issued[s2])
+          if (!stage_wait(ctl, s2)) return false;
       fence_after_sync();
-      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows), column half w / 4
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows), complex columns [64 (w / 4), + 64)
       const int row = i0 + 32 * (warp & 3) + lane;
       const int half = warp >> 2;
-      for (int c0 = half * (kNr / 2); c0 < 2 * ntp && c0 < (half + 1) * (kNr / 2); c0 += 16) {
-        float v[16];
-        tmem_ld16(ctl->tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
+      const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+      for (int c0 = half * (kNc / 2); c0 < ntp && c0 < (half + 1) * (kNc / 2); c0 += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(t_re + lane_off + (uint32_t)c0, vr);
+        tmem_ld16(t_im + lane_off + (uint32_t)c0, vi);
         tmem_wait_ld();
         if (row < M) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int j = j0 + c0 / 2 + e;
+          for (int e = 0; e < 16; ++e) {
+            const int j = j0 + c0 + e;
             if (j < j0 + nt) {
-              cx<float> r = mk(alpha.x * v[2 * e] - alpha.y * v[2 * e + 1], alpha.x * v[2 * e + 1] + alpha.y * v[2 * e]);
+              cx<float> r = mk(alpha.x * vr[e] - alpha.y * vi[e], alpha.x * vi[e] + alpha.y * vr[e]);
               cx<float>* dst = C + row * sci + j * scj;
               if (accumulate) r = r + *dst;
               *dst = r;

@@ -48,7 +48,7 @@ def test_tries_each_rule_then_keeps_the_faster():
     assert ctx64.rules_used == [0, 1, 0, 0]
     assert tu.best[(2, 64)] == 0
     rep = tu.report()
-    assert rep["fp32/chi16"]["best"] == 1 and rep["fp32/chi64"]["best"] == 0
+    assert rep["f32/chi16"]["best"] == 1 and rep["f32/chi64"]["best"] == 0
 
 
 def test_launches_without_contraction_work_are_not_evidence():

@@ -138,17 +138,18 @@ def test_qr_rank_deficient_noise_columns():
 
 def test_emulated_fp64_factorizations_equal_native_fp64():
     """Double-float QR and SVD give the native FP64 results (singular values, the projector U U^H,
-    R up to the column phases of Q) to ~1e-13 on the factorization shapes of the sweeps."""
+    R up to the column phases of Q) on the factorization shapes of the sweeps, to ~1e-11 relative:
+    the 48-bit significand (2^-48 = 3.6e-15 per operation) over O(10^3) operations per entry."""
     lib_ready()
     rng = np.random.default_rng(11)
     for (m, n) in [(128, 64), (64, 128), (128, 128), (32, 16)]:
         A = _rand(rng, m, n) / np.sqrt(n)
         U1, S1, V1 = tjm.selftest_svd(A, 1)
         U2, S2, V2 = tjm.selftest_svd(A, 2)
-        assert np.abs(S1 - S2).max() < 1e-13 * S1[0], (m, n)
+        assert np.abs(S1 - S2).max() < 1e-11 * S1[0], (m, n)
         r = min(m, n) // 2
-        assert np.abs(U1[:, :r] @ U1[:, :r].conj().T - U2[:, :r] @ U2[:, :r].conj().T).max() < 1e-12, (m, n)
+        assert np.abs(U1[:, :r] @ U1[:, :r].conj().T - U2[:, :r] @ U2[:, :r].conj().T).max() < 1e-10, (m, n)
         Q1, R1 = tjm.selftest_qr(A, 1)
         Q2, R2 = tjm.selftest_qr(A, 2)
-        assert np.abs(np.abs(R1) - np.abs(R2)).max() < 1e-13 * np.abs(R1).max(), (m, n)
-        assert np.abs(Q1 @ R1 - Q2 @ R2).max() < 1e-13, (m, n)
+        assert np.abs(np.abs(R1) - np.abs(R2)).max() < 1e-11 * np.abs(R1).max(), (m, n)
+        assert np.abs(Q1 @ R1 - Q2 @ R2).max() < 1e-11, (m, n)
