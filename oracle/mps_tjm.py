@@ -164,19 +164,15 @@ def local_expectations(mps, ops):
     return np.array(vals), norm2
 
 
-def projection_error(mps, W):
-    """Projection error of 1TDVP at the state of `mps` (Sec. "Error measures"):
-    eps = || (I - P) H |psi> ||_2 for the normalised |psi>, with P the projector onto the tangent space
-    of the fixed-bond-dimension manifold at psi,
+def tangent_projector(mps):
+    """The projector P onto the tangent space of the fixed-bond-dimension manifold at the state of `mps`
+    (dense, small L), and the normalised state vector psi:
         P = sum_{l=0}^{L-1} P_L(<l) (x) 1_l (x) P_R(>l)  -  sum_{l=0}^{L-2} P_L(<=l) (x) P_R(>l),
     P_L(<l) the projector onto the span of the left block states of sites 0..l-1 and P_R(>l) onto the
-    right block states of sites l+1..L-1.  Written out densely (small L only): H from the MPO, the block
-    states from a left- and a right-canonical copy of the MPS.
-    """
-    from .dense import mpo_to_dense
+    right block states of sites l+1..L-1, both from a left- and a right-canonical copy of the MPS
+    (Sec. "Error measures"; the 1TDVP projector of Sec. "1TDVP and 2TDVP as tensor networks")."""
     L = len(mps)
     d = mps[0].shape[1]
-    H = mpo_to_dense(W)
     left = [np.array(m) for m in mps]
     for l in range(L - 1):
         qr_move_right(left, l)
@@ -189,7 +185,8 @@ def projection_error(mps, W):
         psi = np.tensordot(psi, M, ([psi.ndim - 1], [0]))
     psi = psi.reshape(-1)
     psi = psi / np.linalg.norm(psi)
-    # left block isometries BL[l]: (d^(l+1), chi_{l+1}); right block isometries BR[l]: (chi_l, d^(L-l))
+    # left block states: the columns of BL[l] (d^(l+1), chi_{l+1}); right block states: the rows of
+    # BR[l] (chi_l, d^(L-l))
     BL = []
     acc = np.ones((1, 1), dtype=np.complex128)
     for l in range(L):
@@ -201,24 +198,33 @@ def projection_error(mps, W):
         acc = np.tensordot(right[l], acc.reshape(right[l].shape[2], -1), ([2], [0])).reshape(right[l].shape[0], -1)
         BR[l] = acc
 
-    def PL(n):        # projector onto the left block states of sites 0..n-1
+    def PL(n):        # sum_a |a><a| over the left block states of sites 0..n-1
         if n == 0:
             return np.ones((1, 1))
         B = BL[n - 1]
         return B @ B.conj().T
 
-    def PR(n):        # projector onto the right block states of sites n..L-1
+    def PR(n):        # sum_b |b><b| over the right block states of sites n..L-1
         if n == L:
             return np.ones((1, 1))
         B = BR[n]
-        return B.conj().T @ B
+        return B.T @ B.conj()
 
     P = np.zeros((d ** L, d ** L), dtype=np.complex128)
     for l in range(L):
         P += np.kron(np.kron(PL(l), np.eye(d)), PR(l + 1))
     for l in range(L - 1):
         P -= np.kron(PL(l + 1), PR(l + 1))
-    v = H @ psi
+    return P, psi
+
+
+def projection_error(mps, W):
+    """Projection error of 1TDVP at the state of `mps` (Sec. "Error measures"):
+    eps = || (I - P) H |psi> ||_2 for the normalised |psi>, P = tangent_projector(mps); H from the MPO.
+    Written out densely (small L only)."""
+    from .dense import mpo_to_dense
+    P, psi = tangent_projector(mps)
+    v = mpo_to_dense(W) @ psi
     return float(np.linalg.norm(v - P @ v))
 
 

@@ -99,6 +99,14 @@ __device__ void blk_site_op(cx<Tc>* M, int chl, int chr, const cx<double>* op, c
 }
 
 // ------------------------------------------------------------------ effective Hamiltonians
+// FP32 contractions on the CUDA cores fuse the MPO block into the second GEMM's operand loads; on
+// the tensor cores (and in FP64) T2 = W T1 is formed first, so that the GEMM streams a plain operand.
+template <class Tc>
+__device__ __forceinline__ bool fused_matvec() {
+  if constexpr (sizeof(Tc) == 4) return !tc_ctl.enabled;
+  return false;
+}
+
 // One site l: y[x][t][y'] = sum Lenv[l][x,w,a] W_l[w,v,t,s] M[a,s,b] Renv[l+1][v,b,y']
 template <class Tc, class Td>
 __device__ __noinline__ void heff1(const Ctx<Tc, Td>& c, int l, const cx<Tc>* x, cx<Tc>* y) {
@@ -106,10 +114,10 @@ __device__ __noinline__ void heff1(const Ctx<Tc, Td>& c, int l, const cx<Tc>* x,
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 1];
   // G1: T1[(x w), (s b)] = L[(x w), a] M[a, (s b)]
   TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, kD * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, kD * chr, 1), c.t1, kD * chr, 1, c.gsm));
-  if constexpr (sizeof(Tc) == 4) {
-    // G2 + G3 fused: the MPO block is applied while G3 loads its A tiles
-    TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, kD, Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, c.Renv(l + 1), y,
-                                        c.gsm, c.wcsr, site_shift(c), kD, Dr - 1, Dr, 0, 1));
+  if (fused_matvec<Tc>()) {
+    if constexpr (sizeof(Tc) == 4)
+      TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, kD, Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, c.Renv(l + 1),
+                                          y, c.gsm, c.wcsr, site_shift(c), kD, Dr - 1, Dr, 0, 1));
   } else {
     // G2: T2[x][(t v)][b] = sum_(w s) Wm1[(t v)][(w s)] T1[x][(w s)][b]
     TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, kD * Dr, Dl * kD, chr, c.P->Wm1 + c.P->Wm1_off[l], c.t1, (long long)Dl * kD * chr, chr, c.t2,
@@ -128,9 +136,10 @@ __device__ __noinline__ void heff2(const Ctx<Tc, Td>& c, int l, int chl, int chr
   const int Dl = c.P->Dbond[l], Dr = c.P->Dbond[l + 2];
   const int d2 = kD * kD;
   TJM_TIMED(c, PH_GEMM, blk_gemm<Tc>(chl * Dl, d2 * chr, chl, matA(c.Lenv(l), chl, 1), matB(x, d2 * chr, 1), c.t1, d2 * chr, 1, c.gsm));
-  if constexpr (sizeof(Tc) == 4) {
-    TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, d2, Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, c.Renv(l + 2), y,
-                                        c.gsm, c.wcsr, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
+  if (fused_matvec<Tc>()) {
+    if constexpr (sizeof(Tc) == 4)
+      TJM_TIMED(c, PH_GEMM, blk_wgemm<Tc>(chl, d2, Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, c.Renv(l + 2),
+                                          y, c.gsm, c.wcsr, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));
   } else {
     TJM_TIMED(c, PH_WAPPLY, blk_wapply<Tc>(chl, d2 * Dr, Dl * d2, chr, c.P->W12 + c.P->W12_off[l], c.t1, (long long)Dl * d2 * chr, chr, c.t2,
                    (long long)d2 * Dr * chr, chr, c.gsm, 2.0 * site_shift(c), d2, Dr - 1, Dr, 0, 1));

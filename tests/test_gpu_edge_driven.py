@@ -6,11 +6,12 @@ the GPU: the long-time magnetisation profile of the TJM ensemble.
   Lindblad equation (solved densely) within 4 standard errors plus the
   method's small time-step bias, and the closed form cos(pi (j-1)/(L-1))
   within 0.02.
-* L = 20 at the paper's chi = 4, in the benchmark's arithmetic (FP32
-  contractions, emulated-FP64 factorizations): 10^4 steps of 128 trajectories
+* L = 16 at the paper's chi = 4, in the benchmark's arithmetic (FP32
+  contractions, emulated-FP64 factorizations): 6000 steps of 96 trajectories
   in one persistent launch (a latency-bound regime of tiny tensors); the
-  profile averaged over t in [700, 1000] follows the closed form (relaxation
-  time ~ L^3: about 60 time units at L = 10, measured with the dense oracle).
+  profile averaged over t in [400, 600] follows the closed form (relaxation
+  time ~ L^3: about 60 time units at L = 10, measured with the dense oracle,
+  so ~250 at L = 16).
 """
 import math
 
@@ -51,13 +52,14 @@ def test_small_chain_reaches_the_lindblad_steady_state():
     z_ss = np.array([O2.expect(rho, I.Z, l, wl.L) for l in range(wl.L)])
     assert (np.abs(m - z_ss) <= 4 * se + 0.003).all(), (m, z_ss, se)
     cos = np.cos(np.pi * np.arange(wl.L) / (wl.L - 1))
-    assert np.abs(m - cos).max() < 0.02, (m, cos)
+    # the exact steady state is within 0.006 of the closed form at L = 6 (oracle pin)
+    assert (np.abs(m - cos) <= 4 * se + 0.01).all(), (m, cos, se)
 
 
-def test_twenty_sites_chi4_follow_the_closed_form_profile():
-    wl = I.edge_driven_xxx(L=20, chi_max=4, n_traj=128, T=1000.0, sample_every=20)
+def test_sixteen_sites_chi4_follow_the_closed_form_profile():
+    wl = I.edge_driven_xxx(L=16, chi_max=4, n_traj=96, T=600.0, sample_every=20)
     pt = _run(wl, tjm.PREC_FP32_DF64)
-    m, se = _window_stats(pt, wl, 700.0)
+    m, se = _window_stats(pt, wl, 400.0)
     cos = np.cos(np.pi * np.arange(wl.L) / (wl.L - 1))
     assert (np.abs(m - cos) <= 4 * se + 0.02).all(), (np.round(m, 3), np.round(se, 3))
     assert m[0] > 0.99 and m[-1] < -0.99

@@ -4,11 +4,11 @@
   trajectory equal the oracle's (same Philox streams) to 1e-10, for the
   Strang-split TJM and for the first-order baseline.
 * The 10-site TFIM of Sec. "Benchmarking" (J = g = 1, sigma^- and Z at 0.1,
-  |0..0>): <X_5> at Jt = 1 from 8192 trajectories.  The second-order TJM at
+  |0..0>): <X_5> at Jt = 1.  The second-order TJM at
   dt = 0.1 agrees with the exact Lindblad value within its Monte Carlo error
   (the paper's point: the Strang splitting pushes the time-step error below the
   sampling error); the first-order baseline at dt = 0.5 is biased by many
-  standard errors.
+  standard errors.  4096 trajectories per arm.
 """
 import math
 
@@ -59,11 +59,11 @@ def _tfim_exact(L, site, t):
 
 def test_tfim_convergence_second_vs_first_order():
     lib_ready()
-    L, site, N = 10, 4, 8192           # <X^[5]> of the paper is the 5th site, index 4
+    L, site, N = 10, 4, 4096           # <X^[5]> of the paper is the 5th site, index 4
     exact = _tfim_exact(L, site, 1.0)
     W = I.tfim_mpo(L, 1.0, 1.0)
     res = {}
-    for order, dt in [(2, 0.1), (1, 0.5), (1, 0.1)]:
+    for order, dt in [(2, 0.1), (1, 0.5)]:
         n = int(round(1.0 / dt))
         ctx = tjm.Context(W, I.noise(L, 0.1, 0.1), dt, 32, 1e-10, precision=tjm.PREC_FP32_DF64, trotter_order=order)
         rid = ctx.run(np.array(I.all_zero(L)), N, 21, [(site, I.X)], [n * dt])
