@@ -134,6 +134,8 @@ typedef struct {
                          * ||(I - P) H |Psi>|| at the measured state (Sec. "Error measures"), computed by
                          * a diagnostic sweep that uses the two-site tangent space (exact for MPOs with
                          * nearest-neighbour terms).  Default 0. */
+  int64_t tc_min_work;  /* with tensor_cores: the smallest GEMM, in complex multiply-adds, that goes to the
+                         * tensor cores (smaller ones stay on the CUDA cores); 0 = 16384 */
 } tjm_options;
 
 /* Fill opts with the defaults above. */

@@ -275,6 +275,7 @@ void tjm_default_options(tjm_options* o) {
   o->tensor_cores = 1;
   o->trotter_order = 2;
   o->projection_error = 0;
+  o->tc_min_work = 0;
 }
 
 const char* tjm_last_error(const tjm_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -295,6 +296,7 @@ tjm_status tjm_create(tjm_ctx** out, const tjm_mpo* H, const tjm_jump* jumps, in
   if (o.tensor_cores < 0 || o.tensor_cores > 1) return fail(nullptr, TJM_EINVAL, "");
   if (o.trotter_order != 1 && o.trotter_order != 2) return fail(nullptr, TJM_EINVAL, "");
   if (o.projection_error < 0 || o.projection_error > 1) return fail(nullptr, TJM_EINVAL, "");
+  if (o.tc_min_work < 0) return fail(nullptr, TJM_EINVAL, "");
   if (o.krylov_max <= 0 || o.krylov_max > 30) o.krylov_max = 30;
   if (!(o.krylov_tol > 0)) o.krylov_tol = o.precision == TJM_PREC_FP64 ? 1e-12 : 1e-7;
   const int L = H->L;
@@ -673,23 +675,24 @@ static tjm_status launch(tjm_ctx* ctx, tjm::SlotDev* const* order, int n, int* n
   tjm_status st = ensure_scratch(ctx, need, ctas);
   if (st) return st;
   TJM_CU(cudaMemsetAsync(next, 0, sizeof(int), ctx->stream));
+  const long long tc_min = ctx->opt.tensor_cores ? (ctx->opt.tc_min_work > 0 ? ctx->opt.tc_min_work : 16384) : 0;
   cudaError_t e;
   switch (ctx->opt.precision) {
     case TJM_PREC_FP64:
       e = tjm::launch_f64(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims, ctx->opt.tensor_cores);
+                          ctx->sdims, tc_min);
       break;
     case TJM_PREC_FP32_DEC32:
       e = tjm::launch_f32d32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                             ctx->scratch_stride, ctx->sdims, ctx->opt.tensor_cores);
+                             ctx->scratch_stride, ctx->sdims, tc_min);
       break;
     case TJM_PREC_FP32_DF64:
       e = tjm::launch_f32df(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                            ctx->scratch_stride, ctx->sdims, ctx->opt.tensor_cores);
+                            ctx->scratch_stride, ctx->sdims, tc_min);
       break;
     default:
       e = tjm::launch_f32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims, ctx->opt.tensor_cores);
+                          ctx->sdims, tc_min);
       break;
   }
   if (e != cudaSuccess) return fail(ctx, TJM_ECUDA, "advance kernel launch: %s", cudaGetErrorString(e));

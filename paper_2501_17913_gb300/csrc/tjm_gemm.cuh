@@ -147,13 +147,12 @@ __device__ __noinline__ void gemm_core(int batch, int M, int N, int K, cx<T> alp
 __shared__ int gemm_tile_rule;
 
 // Tensor-core state of the CTA (tjm_tc.cuh).  When enabled, every FP32 GEMM of
-// at least kTcMinWork complex multiply-adds runs on the tensor cores; smaller
-// ones (chain ends, tiny bonds) stay on the CUDA cores, where one 128-row MMA
-// tile would be mostly padding.
+// at least tc_ctl.min_work complex multiply-adds runs on the tensor cores;
+// smaller ones (chain ends, tiny bonds) stay on the CUDA cores, where one
+// 128-row MMA tile would be mostly padding.
 __shared__ tc::Ctl tc_ctl;
-constexpr long long kTcMinWork = 16384;
 
-__device__ __forceinline__ bool use_tc(long long work) { return tc_ctl.enabled && work >= kTcMinWork; }
+__device__ __forceinline__ bool use_tc(long long work) { return tc_ctl.enabled && work >= tc_ctl.min_work; }
 
 template <class T, bool AK, bool BJ>
 __device__ __forceinline__ void gemm_layout(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* A, int sai,

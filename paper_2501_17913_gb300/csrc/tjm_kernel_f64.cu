@@ -6,12 +6,12 @@
 namespace tjm {
 
 cudaError_t launch_f64(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                        char* scratch, long long stride, ScratchDims dims, int use_tc) {
+                        char* scratch, long long stride, ScratchDims dims, long long tc_min_work) {
   auto kern = advance_kernel<double, double>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<double, double>(true));
   if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<double, double>(use_tc != 0), s>>>(order, n, next, max_steps, scratch, stride, dims,
-                                                                  use_tc);
+  kern<<<ctas, TJM_THREADS, smem_bytes<double, double>(tc_min_work > 0), s>>>(order, n, next, max_steps, scratch, stride,
+                                                                        dims, tc_min_work);
   return cudaGetLastError();
 }
 

@@ -299,17 +299,18 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   __syncthreads();
 }
 
-// use_tc: FP32 contractions on the tensor cores (tcgen05); ignored for FP64
-// contractions.  The CTA holds its tensor-memory accumulator for the whole
-// persistent launch.
+// tc_min_work > 0: FP32 contractions of at least that many complex
+// multiply-adds run on the tensor cores (tcgen05); 0: none (and FP64
+// contractions never).  The CTA holds its tensor-memory accumulator for the
+// whole persistent launch.
 template <class Tc, class Td>
 __global__ void __launch_bounds__(TJM_THREADS, TJM_MIN_BLOCKS)
 advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, char* scratch, long long stride,
-               ScratchDims dims, int use_tc) {
+               ScratchDims dims, long long tc_min_work) {
   extern __shared__ __align__(1024) char smem[];
   __shared__ int sid;
   char* scr = scratch + (long long)blockIdx.x * stride;
-  tc::cta_setup(&tc_ctl, sizeof(Tc) == 4 && use_tc);
+  tc::cta_setup(&tc_ctl, sizeof(Tc) == 4 && tc_min_work > 0, tc_min_work);
   for (;;) {
     if (threadIdx.x == 0) sid = atomicAdd(next, 1);
     __syncthreads();

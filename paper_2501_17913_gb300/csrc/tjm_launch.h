@@ -10,7 +10,7 @@ namespace tjm {
 
 #define TJM_DECLARE_LAUNCH(NAME)                                                                              \
   cudaError_t launch_##NAME(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas, \
-                            char* scratch, long long stride, ScratchDims dims, int use_tc);                               \
+                            char* scratch, long long stride, ScratchDims dims, long long tc_min_work);                               \
   int occupancy_##NAME(int use_tc);
 
 TJM_DECLARE_LAUNCH(f64)

@@ -62,6 +62,7 @@ struct Ctl {
   uint32_t tmem;                 // TMEM base address of this CTA's accumulator
   int failed;                    // a bounded wait ran out: no further MMAs
   int enabled;                   // FP32 contractions go to the tensor cores
+  long long min_work;            // ... from this many complex multiply-adds on
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -151,7 +152,7 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 // ------------------------------------------------------------------ setup / teardown
 // Called by all threads of the CTA at kernel start (after ctl is zeroed is not
 // required: this writes every field).  Warp 0 allocates the accumulator.
-__device__ __forceinline__ void cta_setup(Ctl* ctl, int enabled) {
+__device__ __forceinline__ void cta_setup(Ctl* ctl, int enabled, long long min_work = 16384) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl->bar[s], 1);
@@ -160,6 +161,7 @@ __device__ __forceinline__ void cta_setup(Ctl* ctl, int enabled) {
     }
     ctl->failed = 0;
     ctl->enabled = enabled;
+    ctl->min_work = min_work;
     fence_barrier_init();
   }
   if (enabled && threadIdx.x < 32) tmem_alloc(&ctl->tmem, kTmemCols);

@@ -45,7 +45,7 @@ class tjm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov_max", C.c_int), ("krylov_tol", C.c_double),
                 ("exact_full_bond", C.c_int), ("device", C.c_int), ("max_ctas", C.c_int),
                 ("energy_shift", C.c_int), ("tile_rule", C.c_int), ("tensor_cores", C.c_int),
-                ("trotter_order", C.c_int), ("projection_error", C.c_int)]
+                ("trotter_order", C.c_int), ("projection_error", C.c_int), ("tc_min_work", C.c_int64)]
 
 
 class tjm_stats(C.Structure):
@@ -166,7 +166,7 @@ class Context:
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32_DF64, krylov_max=30, krylov_tol=0.0,
                  exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0, tensor_cores=True,
-                 trotter_order=2, projection_error=False):
+                 trotter_order=2, projection_error=False, tc_min_work=0):
         lib = load()
         self.lib = lib
         L = len(W)
@@ -188,6 +188,7 @@ class Context:
         opt.tensor_cores = int(bool(tensor_cores))
         opt.trotter_order = int(trotter_order)
         opt.projection_error = int(bool(projection_error))
+        opt.tc_min_work = int(tc_min_work)
         self.projection_error = bool(projection_error)
         h = C.c_void_p()
         st = lib.tjm_create(C.byref(h), C.byref(mpo), js, len(jumps), float(dt), int(chi_max), float(trunc_eps),
