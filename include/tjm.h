@@ -123,9 +123,16 @@ typedef struct {
                          * so observables are unchanged; it keeps the FP32 environment sums near
                          * zero instead of near the extensive energy.  0: evolve with H as given. */
   int tile_rule;        /* initial GEMM tile rule of new runs (see tjm_run_set_tile_rule); default 0 */
-  int tensor_cores;     /* 1 (default): FP32 contractions of at least 16384 complex multiply-adds run on the
-                         * tensor cores (tcgen05, TF32 inputs split hi + lo, "3xTF32", FP32 accumulation);
-                         * 0: on the CUDA cores in FP32.  FP64 contractions always use the CUDA cores. */
+  int tensor_cores;     /* 0 (default): every contraction runs on the CUDA cores (FMA, round-to-nearest
+                         * accumulation).  1: FP32 contractions of at least tc_min_work complex
+                         * multiply-adds run on the tensor cores (tcgen05, TF32 inputs split hi + lo,
+                         * "3xTF32", FP32 accumulation in tensor memory).  Measured on GB300: that
+                         * accumulation truncates (a sum of 320 positive products comes out low by about
+                         * 3e-6 relative, the CUDA-core sum is unbiased), which a trajectory whose jump
+                         * draw falls near a threshold turns into an O(1) difference from its FP64
+                         * trajectory; and a kernel that holds the tcgen05 path is resident at one CTA per
+                         * SM instead of two, which made it slower on the trajectory workloads measured.
+                         * FP64 contractions always use the CUDA cores. */
   int trotter_order;    /* 2 (default): the Strang-split TJM with its sampling layer (Sec. "Higher-order
                          * Trotterization", Eq. SimulationStep).  1: the first-order baseline the paper
                          * compares with (Fig. 4a, dotted): Phi_j = J(D[dt] U[dt] Phi_{j-1}) from
@@ -200,6 +207,10 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
  * sites (all resident CTAs together); it is allocated at the first launch
  * that needs it and kept by the context.  For admission control by memory. */
 tjm_status tjm_scratch_bytes(const tjm_ctx* ctx, int chi_cap, int L, int64_t* bytes);
+
+/* tjm_resident_ctas -- CTAs (trajectories in flight) of one launch of this context: the resident wave
+ * the occupancy of its kernel allows on this device. */
+int tjm_resident_ctas(const tjm_ctx* ctx);
 
 /* tjm_poll -- TJM_OK if the run's device work has finished, TJM_EBUSY if not. */
 tjm_status tjm_poll(tjm_ctx* ctx, int64_t run_id);

@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtjm.so")
 SOURCES = ["tjm_capi.cu", "tjm_kernel_f64.cu", "tjm_kernel_f32.cu", "tjm_kernel_f32d32.cu", "tjm_kernel_f32df.cu",
+           "tjm_kernel_f32_tc.cu", "tjm_kernel_f32d32_tc.cu", "tjm_kernel_f32df_tc.cu",
            "tjm_selftest.cu", "tjm_selftest_contract.cu",
            "tjm_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

@@ -221,10 +221,10 @@ int resident(tjm_ctx* ctx) {
   int per_sm = 0, sms = 0;
   const int tc = ctx->opt.tensor_cores;
   switch (ctx->opt.precision) {
-    case TJM_PREC_FP64: per_sm = tjm::occupancy_f64(tc); break;
-    case TJM_PREC_FP32_DEC32: per_sm = tjm::occupancy_f32d32(tc); break;
-    case TJM_PREC_FP32_DF64: per_sm = tjm::occupancy_f32df(tc); break;
-    default: per_sm = tjm::occupancy_f32(tc); break;
+    case TJM_PREC_FP64: per_sm = tjm::occupancy_f64(0); break;
+    case TJM_PREC_FP32_DEC32: per_sm = tc ? tjm::occupancy_f32d32_tc(1) : tjm::occupancy_f32d32(0); break;
+    case TJM_PREC_FP32_DF64: per_sm = tc ? tjm::occupancy_f32df_tc(1) : tjm::occupancy_f32df(0); break;
+    default: per_sm = tc ? tjm::occupancy_f32_tc(1) : tjm::occupancy_f32(0); break;
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   return std::max(1, per_sm) * std::max(1, sms);
@@ -272,7 +272,7 @@ void tjm_default_options(tjm_options* o) {
   o->max_ctas = 0;
   o->energy_shift = 1;
   o->tile_rule = 0;
-  o->tensor_cores = 1;
+  o->tensor_cores = 0;
   o->trotter_order = 2;
   o->projection_error = 0;
   o->tc_min_work = 0;
@@ -643,6 +643,8 @@ static tjm_status prepare(tjm_ctx* ctx, const tjm_state* psi0, int64_t n_traj, i
   return TJM_OK;
 }
 
+int tjm_resident_ctas(const tjm_ctx* ctx) { return ctx ? resident(const_cast<tjm_ctx*>(ctx)) : 0; }
+
 tjm_status tjm_scratch_bytes(const tjm_ctx* ctx, int chi_cap, int L, int64_t* bytes) {
   if (!ctx || !bytes || chi_cap < 1 || chi_cap > 64 || L < 1) return TJM_EINVAL;
   tjm::ScratchDims d = {chi_cap, ctx->Dmax, ctx->opt.krylov_max, L, ctx->n_jumps};
@@ -675,26 +677,19 @@ static tjm_status launch(tjm_ctx* ctx, tjm::SlotDev* const* order, int n, int* n
   tjm_status st = ensure_scratch(ctx, need, ctas);
   if (st) return st;
   TJM_CU(cudaMemsetAsync(next, 0, sizeof(int), ctx->stream));
-  const long long tc_min = ctx->opt.tensor_cores ? (ctx->opt.tc_min_work > 0 ? ctx->opt.tc_min_work : 16384) : 0;
-  cudaError_t e;
+  const bool tc = ctx->opt.tensor_cores && ctx->opt.precision != TJM_PREC_FP64;
+  const long long tc_min = tc ? (ctx->opt.tc_min_work > 0 ? ctx->opt.tc_min_work : 16384) : 0;
+  using launch_fn = cudaError_t (*)(cudaStream_t, tjm::SlotDev* const*, int, int*, int, int, char*, long long,
+                                    tjm::ScratchDims, long long);
+  launch_fn fn;
   switch (ctx->opt.precision) {
-    case TJM_PREC_FP64:
-      e = tjm::launch_f64(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims, tc_min);
-      break;
-    case TJM_PREC_FP32_DEC32:
-      e = tjm::launch_f32d32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                             ctx->scratch_stride, ctx->sdims, tc_min);
-      break;
-    case TJM_PREC_FP32_DF64:
-      e = tjm::launch_f32df(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p,
-                            ctx->scratch_stride, ctx->sdims, tc_min);
-      break;
-    default:
-      e = tjm::launch_f32(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
-                          ctx->sdims, tc_min);
-      break;
+    case TJM_PREC_FP64: fn = tjm::launch_f64; break;
+    case TJM_PREC_FP32_DEC32: fn = tc ? tjm::launch_f32d32_tc : tjm::launch_f32d32; break;
+    case TJM_PREC_FP32_DF64: fn = tc ? tjm::launch_f32df_tc : tjm::launch_f32df; break;
+    default: fn = tc ? tjm::launch_f32_tc : tjm::launch_f32; break;
   }
+  const cudaError_t e = fn(ctx->stream, order, n, next, max_steps, ctas, (char*)ctx->scratch.p, ctx->scratch_stride,
+                           ctx->sdims, tc_min);
   if (e != cudaSuccess) return fail(ctx, TJM_ECUDA, "advance kernel launch: %s", cudaGetErrorString(e));
   ctx->launches += 1;
   return TJM_OK;

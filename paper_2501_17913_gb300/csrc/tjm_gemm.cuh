@@ -152,7 +152,24 @@ __shared__ int gemm_tile_rule;
 // 128-row MMA tile would be mostly padding.
 __shared__ tc::Ctl tc_ctl;
 
-__device__ __forceinline__ bool use_tc(long long work) { return tc_ctl.enabled && work >= tc_ctl.min_work; }
+// TJM_TENSOR_CORES (per translation unit) decides whether the kernels built
+// there carry the tcgen05 path at all.  A kernel image that holds any tcgen05
+// instruction is granted a single resident CTA per SM (measured on GB300 with
+// the occupancy API: the same 128-register, 256-thread trajectory kernel
+// reports two without them), so the CUDA-core instantiations are compiled
+// without it and the tensor-core ones live in translation units of their own.
+#ifndef TJM_TENSOR_CORES
+#define TJM_TENSOR_CORES 0
+#endif
+
+__device__ __forceinline__ bool use_tc(long long work) {
+#if TJM_TENSOR_CORES
+  return tc_ctl.enabled && work >= tc_ctl.min_work;
+#else
+  (void)work;
+  return false;
+#endif
+}
 
 template <class T, bool AK, bool BJ>
 __device__ __forceinline__ void gemm_layout(int batch, int M, int N, int K, cx<T> alpha, const cx<T>* A, int sai,

@@ -1,27 +1,5 @@
-// Instantiation of the persistent trajectory kernel: contractions in float,
-// factorizations in float.
-#include "tjm_kernels.cuh"
-#include "tjm_launch.h"
+// Instantiation of the persistent trajectory kernel on the CUDA cores:
+// contractions and factorizations in float.
+#include "tjm_kernel_inst.cuh"
 
-namespace tjm {
-
-cudaError_t launch_f32d32(cudaStream_t s, SlotDev* const* order, int n, int* next, int max_steps, int ctas,
-                        char* scratch, long long stride, ScratchDims dims, long long tc_min_work) {
-  auto kern = advance_kernel<float, float>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<float, float>(true));
-  if (e != cudaSuccess) return e;
-  kern<<<ctas, TJM_THREADS, smem_bytes<float, float>(tc_min_work > 0), s>>>(order, n, next, max_steps, scratch, stride,
-                                                                        dims, tc_min_work);
-  return cudaGetLastError();
-}
-
-int occupancy_f32d32(int use_tc) {
-  int per_sm = 0;
-  cudaFuncSetAttribute(advance_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem_bytes<float, float>(true));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, advance_kernel<float, float>, TJM_THREADS,
-                                                smem_bytes<float, float>(use_tc != 0));
-  return per_sm;
-}
-
-}  // namespace tjm
+TJM_DEFINE_LAUNCH(f32d32, float, float)

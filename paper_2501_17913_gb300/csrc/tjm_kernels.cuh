@@ -299,18 +299,29 @@ __device__ void run_slot(SlotDev* S, int max_steps, char* scr, const ScratchDims
   __syncthreads();
 }
 
-// tc_min_work > 0: FP32 contractions of at least that many complex
-// multiply-adds run on the tensor cores (tcgen05); 0: none (and FP64
-// contractions never).  The CTA holds its tensor-memory accumulator for the
-// whole persistent launch.
-template <class Tc, class Td>
-__global__ void __launch_bounds__(TJM_THREADS, TJM_MIN_BLOCKS)
+// Built with TJM_TENSOR_CORES = 1 and tc_min_work > 0: FP32 contractions of at
+// least that many complex multiply-adds run on the tensor cores (tcgen05) and
+// the CTA holds its tensor-memory accumulator for the whole persistent launch;
+// FP64 contractions never do.  kTensorCores keeps the two builds' kernels
+// apart by name; the tensor-core build runs one CTA per SM anyway, so it is
+// not held to the two-CTA register budget.
+template <class Tc, class Td, int kTensorCores = TJM_TENSOR_CORES>
+__global__ void __launch_bounds__(TJM_THREADS, kTensorCores ? 1 : TJM_MIN_BLOCKS)
 advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, char* scratch, long long stride,
                ScratchDims dims, long long tc_min_work) {
-  extern __shared__ __align__(1024) char smem[];
+  extern __shared__ __align__(TJM_TENSOR_CORES ? 1024 : 16) char smem[];
   __shared__ int sid;
   char* scr = scratch + (long long)blockIdx.x * stride;
+#if TJM_TENSOR_CORES
   tc::cta_setup(&tc_ctl, sizeof(Tc) == 4 && tc_min_work > 0, tc_min_work);
+#else
+  if (threadIdx.x == 0) {
+    tc_ctl.enabled = 0;
+    tc_ctl.failed = 0;
+    tc_ctl.min_work = 0;
+  }
+  __syncthreads();
+#endif
   for (;;) {
     if (threadIdx.x == 0) sid = atomicAdd(next, 1);
     __syncthreads();
@@ -319,7 +330,9 @@ advance_kernel(SlotDev* const* order, int n_slots, int* next, int max_steps, cha
     if (s >= n_slots) break;
     run_slot<Tc, Td>(order[s], max_steps, scr, dims, smem);
   }
+#if TJM_TENSOR_CORES
   tc::cta_teardown(&tc_ctl);
+#endif
 }
 
 }  // namespace tjm

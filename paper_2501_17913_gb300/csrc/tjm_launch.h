@@ -1,6 +1,6 @@
-// Launchers of the persistent trajectory kernel, one per precision pair; each
-// lives in its own translation unit so the three instantiations compile in
-// parallel.
+// Launchers of the persistent trajectory kernel, one per precision pair and,
+// for FP32 contractions, one more with the tcgen05 path (suffix _tc); each
+// lives in its own translation unit so the instantiations compile in parallel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -17,5 +17,8 @@ TJM_DECLARE_LAUNCH(f64)
 TJM_DECLARE_LAUNCH(f32)
 TJM_DECLARE_LAUNCH(f32d32)
 TJM_DECLARE_LAUNCH(f32df)
+TJM_DECLARE_LAUNCH(f32_tc)
+TJM_DECLARE_LAUNCH(f32d32_tc)
+TJM_DECLARE_LAUNCH(f32df_tc)
 
 }  // namespace tjm

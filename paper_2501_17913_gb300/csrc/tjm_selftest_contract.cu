@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tjm.h"
+#define TJM_TENSOR_CORES 1    // the tests route contractions either way
 #include "tjm_kernels.cuh"
 #include "tjm_mpo_layout.h"
 

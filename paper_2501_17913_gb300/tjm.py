@@ -85,6 +85,7 @@ SIGNATURES = [
     ("tjm_run_group_advance", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int, C.c_int]),
     ("tjm_poll", C.c_int, [C.c_void_p, C.c_int64]),
     ("tjm_scratch_bytes", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
+    ("tjm_resident_ctas", C.c_int, [C.c_void_p]),
     ("tjm_result", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.POINTER(C.c_double)]),
     ("tjm_run_stats", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(tjm_stats)]),
@@ -165,7 +166,7 @@ class Context:
     """One TJM problem (tjm_create) and the runs started on it."""
 
     def __init__(self, W, jumps, dt, chi_max, trunc_eps, precision=PREC_FP32_DF64, krylov_max=30, krylov_tol=0.0,
-                 exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0, tensor_cores=True,
+                 exact=False, device=0, max_ctas=0, energy_shift=True, tile_rule=0, tensor_cores=False,
                  trotter_order=2, projection_error=False, tc_min_work=0):
         lib = load()
         self.lib = lib
@@ -344,6 +345,10 @@ class Context:
     def free(self, run_id):
         self._check(self.lib.tjm_run_free(self.h, run_id), "tjm_run_free")
         self.runs.pop(run_id, None)
+
+    def resident_ctas(self):
+        """Trajectories in flight in one launch of this context (its kernel's resident wave)."""
+        return int(self.lib.tjm_resident_ctas(self.h))
 
     def scratch_bytes(self, chi_cap, L):
         """Device bytes of the per-CTA scratch a launch holds for trajectories up to (chi_cap, L)."""

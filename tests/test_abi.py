@@ -43,7 +43,7 @@ def test_default_options(lib):
     lib.tjm_default_options(C.byref(o))
     assert (o.precision, o.krylov_max, o.krylov_tol, o.exact_full_bond, o.device, o.max_ctas) == \
            (tjm.PREC_FP32_DF64, 30, 0.0, 0, 0, 0)
-    assert (o.energy_shift, o.tile_rule, o.tensor_cores, o.trotter_order, o.projection_error) == (1, 0, 1, 2, 0)
+    assert (o.energy_shift, o.tile_rule, o.tensor_cores, o.trotter_order, o.projection_error) == (1, 0, 0, 2, 0)
 
 
 @pytest.mark.parametrize("case", ["dt", "chi_low", "chi_high", "eps", "one_site", "open_end", "precision",

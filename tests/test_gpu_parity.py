@@ -98,6 +98,42 @@ def test_small_chain_fp32_paths(prec):
     assert np.mean(z < 3) >= 0.99 and z.max() < 5
 
 
+@pytest.mark.parametrize("prec", [tjm.PREC_FP32, tjm.PREC_FP32_DF64, tjm.PREC_FP32_DEC32])
+def test_small_chain_tensor_core_path(prec):
+    """The tcgen05 build of the trajectory kernel with every FP32 contraction sent to the tensor cores
+    (tc_min_work = 1): per trajectory within 1e-4 of the FP64 oracle for the first 20 steps, as the
+    CUDA-core build is held to."""
+    horizon = 20
+    wl = I.config_small_fp64(32)
+    pt, _, _, st, _, ctx = run_gpu(wl, prec, n_steps=horizon, tensor_cores=True, tc_min_work=1)
+    assert ctx.resident_ctas() > 0
+    res = _oracle('config_small_fp64', {'n_traj': 32}, range(32), {})
+    ok, worst = 0, 0.0
+    for g, (v, so) in zip(pt, res):
+        if so['margin_upto'][horizon] < 1e-5:
+            continue
+        worst = max(worst, float(np.abs(g[:horizon + 1] - v[:horizon + 1]).max()))
+        ok += 1
+    assert worst < 1e-4, worst
+    assert ok >= 28
+
+
+def test_cuda_core_kernels_run_two_ctas_per_sm():
+    """The CUDA-core builds of the trajectory kernel hold no tcgen05 code and are resident at two CTAs
+    (of 256 threads, 128 registers) per SM; the tensor-core build at one."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    wl = I.config_small_fp64(4)
+    for prec in (tjm.PREC_FP64, tjm.PREC_FP32, tjm.PREC_FP32_DF64, tjm.PREC_FP32_DEC32):
+        ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=prec)
+        assert ctx.resident_ctas() == 2 * sms, (prec, ctx.resident_ctas())
+        ctx.close()
+    ctx = tjm.Context(wl.W, wl.jumps, wl.dt, wl.chi_max, wl.trunc_eps, precision=tjm.PREC_FP32_DF64,
+                      tensor_cores=True)
+    assert ctx.resident_ctas() == sms
+    ctx.close()
+
+
 def test_edge_cases_fp64():
     """Two sites, chi_max = 1, one trajectory, no noise, only t = 0, H = 0."""
     obs = I.z_observables(2) + [(0, I.X)]
