@@ -46,13 +46,13 @@ def parse():
     p.add_argument("--ntraj", type=int, default=256)
     p.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 GPU arm")
     p.add_argument("--fp64-traj", type=int, default=0,
-                   help="trajectories of the plain-FP64 GPU arm (0: one per SM; see DESIGN, FP64 is pipe-bound)")
-    p.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end tjm_run measurement")
+                   help="trajectories of the plain-FP64 GPU arm (0: one per SM, at most the main arm's count)")
+    p.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end tjm_run measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--serve-requests", type=int, default=8,
                    help="serving replay: the first R arrivals of the Poisson request stream (0: skip)")
     p.add_argument("--serve-traj-scale", type=float, default=1.0 / 64)
-    p.add_argument("--serve-max-steps", type=int, default=10)
+    p.add_argument("--serve-max-steps", type=int, default=5)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--ref-sites", type=int, default=200,
                    help="reference arm: sites of the chi-saturated chain each oracle trajectory steps through")
@@ -303,6 +303,7 @@ def main():
     obs = I.z_observables(L)
     psi = I.random_mps(L, chi, 2025)
     times = [dt * j for j in range(n_total + 1)]
+    t_main = time.perf_counter()
     ctx = tjm.Context(W, jumps, dt, chi, 1e-10, precision=prec, device=local)
     rid = ctx.prepare(psi, N, 0, obs, times, first_traj=rank * N)
     stream = torch.cuda.ExternalStream(ctx.stream())
@@ -333,6 +334,7 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     s1 = ctx.stats(rid)
+    t_main = time.perf_counter() - t_main
     gpu_launches = ctx.launches() - launches0   # trajectory-kernel launches (each preceded by a counter memset)
     from paper_2501_17913_gb300.shard import job_rate
     value, t_max = job_rate(N * L * a.steps, ms)       # all ranks' units over the slowest rank's time
@@ -377,7 +379,10 @@ def main():
     roof["phase_share"] = {k: cyc[k] / tot_cyc for k in ("gemm", "mpo_contract", "lanczos", "qr", "svd", "matvec",
                                                          "krylov_expm", "tdvp", "dissipate_jump", "env_build",
                                                          "measure")}
+    ctx.close()                              # frees the trajectory state before the other arms allocate theirs
+    ctx = None
     extra = {}
+    phase_wall = {}
     # end to end through the C ABI with host buffers: tjm_run (init + F_0 + K steps) and tjm_result
     if not a.no_e2e:
         ke = max(1, min(a.steps, a.e2e_steps))
@@ -394,12 +399,18 @@ def main():
                "d2h_bytes_per_step": d2h // ke, "wall_s": t_e2e, "steps": ke,
                "note": "tjm_run from host inputs (upload, init, F_0, %d steps) + tjm_result to host" % ke}
         ctx2.close()
+        phase_wall["e2e"] = t_e2e
     else:
         e2e = None
     # plain FP64 GPU path on the same workload (L, chi, H, noise, dt, random chi-saturated start): one timed step
     if not a.no_fp64 and rank == 0:
-        N64 = a.fp64_traj or n_sm
+        t3 = time.perf_counter()
         ctx3 = tjm.Context(W, jumps, dt, chi, 1e-10, precision=tjm.PREC_FP64, device=local)
+        # FP64 is bound by the SM's FP64 pipe: one CTA per SM already takes nearly all of it (measured at
+        # L = 100: 152 trajectories 669, 304 trajectories 692 trajectory*site*steps/s), while a count between
+        # one and two per SM leaves the two-CTA SMs setting the step time.  One trajectory per SM is the
+        # FP64 path's best use of the GPU per unit of time.
+        N64 = a.fp64_traj or min(N, n_sm)
         r3 = ctx3.prepare(psi, N64, 0, obs, [dt, 2 * dt])
         ctx3.advance(r3, 0)
         ctx3.sync()
@@ -416,12 +427,17 @@ def main():
                                       "bench's seed), FP64 contractions and factorizations" % (N64, L, chi),
                              "ms": ms64}
         ctx3.close()
+        phase_wall["fp64_arm"] = time.perf_counter() - t3
     serving = None
     if a.serve_requests > 0 and rank == 0:
+        t4 = time.perf_counter()
         serving = run_serving(a, prec, local)
+        phase_wall["serving"] = time.perf_counter() - t4
     cpu = None
     if not a.no_cpu and rank == 0:
+        t5 = time.perf_counter()
         cpu = oracle_sample(max(1, min(os.cpu_count() or 1, 16)), min(L, a.ref_sites), chi)
+        phase_wall["cpu_baseline"] = time.perf_counter() - t5
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -440,11 +456,11 @@ def main():
                          "matvecs_bond": s1["matvec_bond"] - s0["matvec_bond"],
                          "matvecs_two_site": s1["matvec_two_site"] - s0["matvec_two_site"],
                          "contract_gflop": fc / 1e9, "decomp_gflop": fd / 1e9}}
+        out["wall_s"] = dict(phase_wall, main_arm=t_main)
         if "fp64_gpu" in extra:
             out["fp64_gpu"] = extra["fp64_gpu"]
             out["vs_fp64_gpu"] = value / world / extra["fp64_gpu"]["value"]
         print(json.dumps(out), flush=True)
-    ctx.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

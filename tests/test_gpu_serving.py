@@ -28,10 +28,11 @@ def _requests():
 def test_results_in_the_mix_equal_results_alone(budget):
     lib_ready()
     reqs = _requests()
-    mem = None
+    srv = Server(precision=tjm.PREC_FP32_DEC32, mem_budget=None, steps_per_tick=1, keep_per_traj=True)
     if budget == "tight":
-        mem = max(state_bytes(wl, tjm.PREC_FP32_DEC32) for _, wl in reqs) * 2   # forces queueing for memory
-    srv = Server(precision=tjm.PREC_FP32_DEC32, mem_budget=mem, steps_per_tick=1, keep_per_traj=True)
+        # the launch scratch for the largest request plus two requests' state: forces queueing for memory
+        scratch = srv.anchor.scratch_bytes(max(wl.chi_max for _, wl in reqs), max(wl.L for _, wl in reqs))
+        srv.budget = scratch + 2 * max(state_bytes(wl, tjm.PREC_FP32_DEC32) for _, wl in reqs)
     t0 = time.perf_counter()
     for t_arr, wl in reqs:
         srv.submit(wl, t0 + t_arr)
