@@ -39,7 +39,6 @@ template <class Tc, class Td> struct Ctx {
   cx<Tc>* krylov; cx<Tc>* w; cx<Tc>* t1; cx<Tc>* t2; cx<Tc>* theta; cx<Tc>* tmp; cx<Tc>* bond;
   cx<Tc>* E; cx<Tc>* F;
   cx<Td>* da; cx<Td>* du; cx<Td>* dv; cx<Td>* dvw; cx<Td>* drd; Td* dtau; Td* ds; int* iw;
-  long long dcap;        // complex elements in each of da, du and dv
   cx<double>* G;         // [L][4] per-site reduced 2x2 blocks
   cx<double>* G2;        // [L][16] reduced 4x4 blocks of sites (l, l+1) where a two-site observable starts
   double* wts;           // jump weights
@@ -515,36 +514,9 @@ __device__ __noinline__ int svd_of(const Ctx<Tc, Td>& c, int m, int n, const cx<
   __syncthreads();
   // on the work matrix: Wk = Uw diag(s) Vw^H; Uw -> du (mm x nn), Vw -> dv (nn x nn)
   int sweeps = 0;
-  // QR-preconditioned Jacobi for the FP64 / double-float factorizations in global memory: Wk = Q R,
-  // then one-sided Jacobi on X = R^H (nn x nn): X Vx = Ux diag(s), so Wk = (Q Vx) diag(s) Ux^H, i.e.
-  // Uw = Q Vx and Vw = Ux.  On the graded spectra of an MPS bond, Jacobi on R^H needs about a third of
-  // the sweeps it needs on Wk itself, over columns of length nn instead of mm.  Buffers: Q in
-  // da[0, mm nn), R in dv, X in du, Vx behind Q in da, Uw into du at the end.  The test depends on
-  // this trajectory's own bond cap only (the buffers are sized for the largest cap of all runs
-  // resident on the context), so a trajectory takes the same path alone and in a mixed batch.
-  const long long own_cap = 4LL * c.S->chi_cap * c.S->chi_cap;
-  const bool pre = !in_smem && sizeof(Td) == 8 && nn >= 2 && (long long)nn * (mm + nn) <= own_cap &&
-                   own_cap <= c.dcap;
-  if (pre) {
-    TJM_TIMED(c, PH_SVD, {
-      blk_qr<Td>(mm, nn, a, a, c.dv, c.drd, c.dtau, c.red);
-      __syncthreads();
-      for (int e = threadIdx.x; e < nn * nn; e += TJM_THREADS)    // X[i, j] = conj(R[j, i])
-        c.du[e] = conj(c.dv[(long long)(e % nn) * nn + e / nn]);
-      __syncthreads();
-      cx<Td>* vx = a + (long long)mm * nn;
-      sweeps = blk_svd_jacobi<Td>(nn, nn, c.du, c.dv, c.ds, vx, c.dvw, reinterpret_cast<Td*>(c.dvw + (long long)nn * nn),
-                                  c.iw, c.red, c.P->exact != 0);
-      blk_gemm_cm<Td>(mm, nn, nn, a, vx, c.du);
-    });
-    // Householder QR with explicit Q, the Jacobi sweeps on the nn x nn factor, and Q Vx
-    count_decomp(c, 4.0 * ((double)mm * nn * nn - (double)nn * nn * nn / 3.0) +
-                        (double)(sweeps + 1) * 0.5 * nn * (nn - 1) * (3.0 * nn + 4.0 * nn) + (double)mm * nn * nn);
-  } else {
-    TJM_TIMED(c, PH_SVD, sweeps = blk_svd_jacobi<Td>(mm, nn, a, c.du, c.ds, c.dv, vw, sv, c.iw, c.red, c.P->exact != 0));
-    // per sweep and pair: three column dot products and two column rotations (A and V)
-    count_decomp(c, (double)(sweeps + 1) * 0.5 * nn * (nn - 1) * (3.0 * mm + 2.0 * (mm + nn)));
-  }
+  TJM_TIMED(c, PH_SVD, sweeps = blk_svd_jacobi<Td>(mm, nn, a, c.du, c.ds, c.dv, vw, sv, c.iw, c.red, c.P->exact != 0));
+  // per sweep and pair: three column dot products and two column rotations (A and V)
+  count_decomp(c, (double)(sweeps + 1) * 0.5 * nn * (nn - 1) * (3.0 * mm + 2.0 * (mm + nn)));
   if (tr) {
     // A = (Wk)^H = Vw diag(s) Uw^H : U = Vw (m x nn), V = Uw (n x nn); swap buffers by copy
     for (long long e = threadIdx.x; e < (long long)mm * nn; e += TJM_THREADS) c.da[e] = c.du[e];

@@ -112,7 +112,6 @@ __device__ void make_ctx(Ctx<Tc, Td>& c, SlotDev* S, char* scr, const ScratchDim
   c.dtau = reinterpret_cast<Td*>(scr + mp.dtau);
   c.ds = reinterpret_cast<Td*>(scr + mp.ds);
   c.iw = reinterpret_cast<int*>(scr + mp.iw);
-  c.dcap = 4LL * dims.chi_cap * dims.chi_cap;
   c.G = reinterpret_cast<cx<double>*>(scr + mp.G);
   c.G2 = reinterpret_cast<cx<double>*>(scr + mp.G2);
   c.wts = reinterpret_cast<double*>(scr + mp.wts);

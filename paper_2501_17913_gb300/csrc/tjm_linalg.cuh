@@ -228,29 +228,6 @@ __device__ __noinline__ void blk_cgs_perm(int len, int n, cx<T>* q, const int* p
   }
 }
 
-// C (m x n) = A (m x k) B (k x n), all column-major (leading dimensions m, k
-// and m), in the factorization precision.  Each thread forms four output
-// columns of one row at a time; the operands are read through L1.
-template <class T>
-__device__ __noinline__ void blk_gemm_cm(int m, int n, int k, const cx<T>* A, const cx<T>* B, cx<T>* C) {
-  const int nb = (n + 3) / 4;
-  for (long long e = threadIdx.x; e < (long long)m * nb; e += TJM_THREADS) {
-    const int i = (int)(e % m), j0 = 4 * (int)(e / m);
-    const int nj = n - j0 < 4 ? n - j0 : 4;
-    cx<T> acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-    for (int p = 0; p < k; ++p) {
-      const cx<T> x = A[(long long)p * m + i];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (t < nj) cfma(acc[t], x, B[(long long)(j0 + t) * k + p]);
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (t < nj) C[(long long)(j0 + t) * m + i] = acc[t];
-  }
-  __syncthreads();
-}
-
 // ------------------------------------------------------------------ Jacobi SVD
 // a: mm x nn column-major with mm >= nn (the caller transposes when needed).
 // On exit: u (mm x nn) orthonormal columns sorted by decreasing singular
