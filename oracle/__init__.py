@@ -16,8 +16,10 @@ dense      O2: the same Strang-ordered jump schedule on a dense state vector,
 
 Pins (tests/test_oracle_pins.py, tests/test_oracle_ensemble.py) fix every part
 against closed forms, library routines on special cases, dense computations or
-exactly solvable limits, with one exception: the TDVP sweep below full bond
-dimension (mps_tjm.Sweeper with truncation) is parity unpinned -- no closed form
-exists; it is checked only by its exactness at full bond dimension and by its
-monotone convergence to the dense evolution as chi_max grows.
+exactly solvable limits, with one exception: the TDVP sweep when a two-site
+block's rank exceeds chi_max and is truncated (mps_tjm.Sweeper) is parity
+unpinned -- no closed form exists; it is checked by its exactness at full bond
+dimension, by exact update counts and exact norm and energy conservation of the
+dynamic switch where nothing is truncated, and by its monotone convergence to
+the dense evolution as chi_max grows.
 """

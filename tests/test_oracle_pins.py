@@ -240,6 +240,64 @@ def test_one_site_tdvp_conserves_norm_and_energy():
     assert abs(e1 - e0) < 1e-10
 
 
+def _prepared(L, bonds, seed):
+    mps = _random_mps(L, bonds, seed)
+    for l in range(L - 1, 0, -1):
+        O1.rq_move_left(mps, l)
+    mps[0] /= np.linalg.norm(mps[0])
+    return mps
+
+
+def test_dynamic_tdvp_switch_is_per_bond_and_exact_without_truncation():
+    """The dynamic switch of Sec. "Dynamic TDVP": a two-site update exactly where the bond is below
+    chi_max, a one-site update elsewhere.  Bonds [1, 2, 4, 4, 4, 2, 1] at chi_max = 4: the two edge
+    bonds are below chi_max but already at full rank (2), so each sweep makes 2 two-site and 3
+    one-site updates per half sweep, none truncates, and every substep is the exponential of a
+    Hermitian effective operator or an exact refactorization: norm and energy are conserved to the
+    Lanczos accuracy.  Testing `<=` instead of `<` would make every update two-site and truncate."""
+    L = 6
+    W = I.xxx_mpo(L, 1.0, 0.5)
+    H = O2.mpo_to_dense(W)
+    mps = _prepared(L, [1, 2, 4, 4, 4, 2, 1], 13)
+    prob = O1.Problem(W, [], 0.1, chi_max=4)
+    sw = O1.Sweeper(prob)
+    sw.build_right_envs(mps)
+    e0, _ = _energy(mps, H)
+    for _ in range(3):
+        sw.sweep(mps, 0.05)
+        sw.build_right_envs(mps)
+    e1, n1 = _energy(mps, H)
+    assert sw.updates == {'two_site': 3 * 4, 'one_site': 3 * 6}, sw.updates
+    assert [m.shape[2] for m in mps] == [2, 4, 4, 4, 2, 1]
+    assert abs(n1 - 1.0) < 1e-11
+    assert abs(e1 - e0) < 1e-10
+
+
+def test_dynamic_tdvp_bonds_grow_to_chi_max_without_truncation():
+    """From bonds of 2 everywhere with chi_max = 4, the left-to-right half sweep is two-site at all
+    five bonds; a two-site block between two bonds of 2 has rank <= 4, so the interior bonds grow
+    to 4 (generic state) without any truncation.  The switch is taken when the sweep reaches a
+    bond, so the right-to-left half sweep finds the three interior bonds at chi_max (one-site) and
+    the two full-rank edge bonds at 2 (two-site).  Norm and energy are conserved.  Keeping the old
+    bond dimension, or truncating below chi_max, would leave the bonds at 2 or change the energy."""
+    L = 6
+    W = I.xxx_mpo(L, 1.0, 0.5)
+    H = O2.mpo_to_dense(W)
+    mps = _prepared(L, [1, 2, 2, 2, 2, 2, 1], 17)
+    prob = O1.Problem(W, [], 0.1, chi_max=4)
+    sw = O1.Sweeper(prob)
+    sw.build_right_envs(mps)
+    e0, _ = _energy(mps, H)
+    sw.sweep(mps, 0.05)
+    sw.build_right_envs(mps)
+    e1, n1 = _energy(mps, H)
+    bonds = [m.shape[2] for m in mps[:-1]]
+    assert sw.updates == {'two_site': 5 + 2, 'one_site': 3}, sw.updates
+    assert bonds[0] == 2 and bonds[-1] == 2 and max(bonds) == 4 and all(b <= 4 for b in bonds), bonds
+    assert abs(n1 - 1.0) < 1e-11
+    assert abs(e1 - e0) < 1e-10
+
+
 def test_padded_product_state_is_right_canonical_and_exact():
     phis = I.haar_product(5, np.random.default_rng(4))
     mps = O1.padded_product_mps(phis)
