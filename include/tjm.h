@@ -209,7 +209,8 @@ tjm_status tjm_run_group_advance(tjm_ctx* const* ctxs, const int64_t* run_ids, i
 tjm_status tjm_scratch_bytes(const tjm_ctx* ctx, int chi_cap, int L, int64_t* bytes);
 
 /* tjm_resident_ctas -- CTAs (trajectories in flight) of one launch of this context: the resident wave
- * the occupancy of its kernel allows on this device. */
+ * the occupancy of its kernel allows on this device, before the max_ctas cap (two per SM for the
+ * CUDA-core builds, one per SM for the tensor-core build).  0 for a null context. */
 int tjm_resident_ctas(const tjm_ctx* ctx);
 
 /* tjm_poll -- TJM_OK if the run's device work has finished, TJM_EBUSY if not. */
