@@ -89,10 +89,11 @@ def _sampled_runs(wl, g, prec, extra=0):
 
 
 def _fp64_l30(g, wl):
-    """FP64 on the L=30 chain, computed once: the 32 sampled trajectories plus 224 more, all in one
-    launch (one resident wave, so the ensemble costs no more time than the sampled trajectories)."""
+    """FP64 on the L=30 chain, computed once: the 32 sampled trajectories plus 272 more, all in one
+    launch (one resident wave of 304 CTAs, so the ensemble costs no more time than the sampled
+    trajectories)."""
     if "l30_fp64" not in _CACHE:
-        pt, ptx, stx = _sampled_runs(wl, g, tjm.PREC_FP64, extra=224)
+        pt, ptx, stx = _sampled_runs(wl, g, tjm.PREC_FP64, extra=272)
         _check_properties(ptx, stx, wl.chi_max)
         allv = np.concatenate([np.array([pt[int(t)] for t in g['traj']]), ptx])
         _CACHE["l30_fp64"] = (pt, allv.mean(axis=0), allv.std(axis=0, ddof=1) / np.sqrt(len(allv)))
@@ -116,7 +117,7 @@ def test_l30_sampled_trajectories_to_horizon(prec):
 def test_l30_1024_trajectories_ensemble_fp32_vs_fp64(prec):
     """All 1024 L=30 trajectories for 100 steps in the benchmark's arithmetic: properties of every
     trajectory, the sampled ones to the horizon, and the ensemble mean within 3 standard errors of an
-    FP64 ensemble of 256 trajectories (FP64 runs at GB300's FP64 rate; the combined standard error
+    FP64 ensemble of 304 trajectories (FP64 runs at GB300's FP64 rate; the combined standard error
     accounts for the smaller sample).  The all-FP32 mode is checked per trajectory above."""
     g = _gold("l30")
     wl = I.config_l30()
