@@ -107,7 +107,9 @@ class Server:
                 still.append(r)
                 continue
             if self.used + r.bytes + self._scratch_need(r.wl) > self.budget and self.active:
-                still.append(r)          # wait for memory; admit in arrival order
+                # waits for memory; later arrivals that fit are still admitted (backfilling), and a
+                # request is always admitted once nothing else runs, so none waits forever
+                still.append(r)
                 continue
             wl = r.wl
             rule = self.tuner.best.get((int(self.precision), int(wl.chi_max)), 0) if self.tuner else 0

@@ -124,3 +124,38 @@ def test_arrivals_in_the_future_wait():
         pass
     assert len(srv.finished) == 2 and srv.finished[1].admitted >= 5.0
     srv.close()
+
+
+def test_replay_of_the_first_200_arrivals_of_the_request_stream():
+    """C5's finite replay on the stand-in: the first 200 arrivals of the Poisson stream (20/s, seed 11),
+    trajectory counts scaled by 1/64 and at most 5 steps each, under a 20 GB budget.  Every request
+    finishes after it arrived, memory stays within the budget (or one oversize request running
+    alone), requests that arrive while others run join the running batch, and the report is
+    consistent."""
+    import math
+    clk = Clock()
+    be = FakeBackend(clk)
+    budget = 20 * 10 ** 9
+    srv = serve.Server(mem_budget=budget, backend=be, clock=clk)
+    stream = I.request_stream()[:200]
+    biggest = 0
+    for t_arr, wl in stream:
+        wl.n_traj = max(1, int(math.ceil(wl.n_traj / 64)))
+        wl.n_steps = min(wl.n_steps, 5)
+        wl.sample_steps = [wl.n_steps]
+        biggest = max(biggest, serve.state_bytes(wl, srv.precision))
+        srv.submit(wl, arrival=t_arr)
+    while srv.tick():
+        assert srv.used <= max(budget, biggest)
+        if not srv.active and srv.queue:       # idle until the next arrival: the stand-in clock jumps
+            clk.t = max(clk.t, min(q.arrival for q in srv.queue))
+    done = srv.finished
+    assert len(done) == 200 and srv.used == 0 and not srv.queue
+    assert all(r.admitted >= r.arrival and r.done > r.admitted for r in done)
+    assert all(r.ctx.closed for r in done)
+    assert any(a.admitted > b.admitted and a.admitted < b.done for a in done for b in done if a is not b)
+    rep = srv.report(0.0, clk.t)
+    assert rep["requests"] == 200 and rep["launches"] == len(be.launches)
+    assert rep["p99_latency_s"] >= rep["p50_latency_s"] > 0
+    assert rep["sustained"] > 0 and rep["offered"] > rep["sustained"]
+    srv.close()
